@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Benchmark of the SPH sloshing step on the large tank.
+
+Workload: R = 0.5 m, 50 % fill, dx = 0.002 m (97,748 fluid + 4,741 ghost
+particles), dt = 5e-5 s, bang-bang slew torque input, grid rebuilt every
+step.  One benchmark step = ``--inner`` inner SPH steps (default 1000)
+replayed from captured CUDA graphs; L2 is flushed between benchmark steps.
+
+Metric: pair interactions per second (ordered fluid pairs with r < 2h plus
+fluid-ghost pairs with r < h, counted exactly by the force kernel).
+
+Arms:
+  default            the CUDA library; prints one JSON line (rank 0).
+  --impl reference   the FP64 CPU oracle on the host cores, on bounded
+                     samples of the same workload (rank 0 only).
+Multi-GPU (torchrun): the single tank does not shard, so every rank runs an
+independent replica ("replicas only"); value = all ranks' pairs / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "SPH pair-interactions/s at 100k particles; surrogate vs SPH sims/s at NRMSE<=5%"
+UNIT = "pair-interactions/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--inner", type=int, default=1000, help="inner SPH steps per benchmark step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--relax", type=int, default=40000, help="damped relaxation steps before timing")
+    return ap.parse_args()
+
+
+def _workload(inner):
+    from paper_2604_12505_gb300 import workloads as W
+    cfg = dict(W.LARGE)
+    desc = {
+        "workload": "large tank: R=0.5 m, fill 0.5, dx=0.002 m, 97,748 fluid + 4,741 ghost particles, "
+                    f"dt=5e-5 s, bang-bang slew torque, {inner} inner steps per step",
+        "inner_steps_per_step": inner,
+        "l2": "flushed between steps (256 MiB write)",
+        "initial_state": "lattice relaxed to rest with damping 2e-3 per step, tank held fixed",
+        "particles_fp32_body_fp64": True,
+    }
+    return cfg, desc
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = str(gpu_index)
+        self.rows = []
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.p = None
+
+    def _read(self):
+        for line in self.p.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9 and f[0] == self.idx:
+                self.rows.append(f)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[5 + i]})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# Algorithmic bytes per launch of each kernel (compulsory traffic of the
+# data structures the kernel must read or write once):
+#   density  per particle 28 B (16 pv + 4 index + 8 rho/P out) + per cell 8 B (count read, next count clear)
+#            + per ghost 48 B (16 body-frame position in, 32 world position / velocity out)
+#   force    per particle 52 B (16 pv + 4 index + 8 rho/P in; 16 pv + 4 index out; 4 count claim)
+#            + per cell 4 B + per ghost 32 B
+def algorithmic_bytes(n_f, n_g, n_cells):
+    return {"density": 28 * n_f + 8 * n_cells + 48 * n_g,
+            "force": 52 * n_f + 4 * n_cells + 32 * n_g}
+
+
+# --------------------------------------------------------------------------
+def cpu_baseline(cfg, seconds: float):
+    from oracle import sph as orc
+    from paper_2604_12505_gb300 import workloads as W
+    p = orc.params(**cfg)
+    x, gB = orc.tank(p)
+    v = np.zeros_like(x)
+    body = np.zeros(6)
+    pairs = orc.pair_count(p, x, gB, body)
+    u = W.bang_bang_slew(1, cfg["dt"])
+    t0 = time.perf_counter()
+    n = 0
+    while True:
+        x, v, body, _, _ = orc.run(p, x, v, gB, body, 1, u=u, record=False)
+        n += 1
+        if time.perf_counter() - t0 >= seconds or n >= 500:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": pairs * n / dt, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+            "sample": f"{n} FP64 oracle steps of the large tank ({pairs} pairs per step), {dt:.1f} s"}
+
+
+def run_reference(a):
+    per = 20  # oracle steps per benchmark step (a bounded sample of the workload)
+    cfg, desc = _workload(per)
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import sph as orc
+    from paper_2604_12505_gb300 import workloads as W
+    p = orc.params(**cfg)
+    x, gB = orc.tank(p)
+    v = np.zeros_like(x)
+    body = np.zeros(6)
+    pairs = orc.pair_count(p, x, gB, body)
+    u = W.bang_bang_slew(per, cfg["dt"])
+    for _ in range(a.warmup):
+        x, v, body, _, _ = orc.run(p, x, v, gB, body, 1, u=u[:1], record=False)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        x, v, body, _, _ = orc.run(p, x, v, gB, body, per, u=u, record=False)
+    T = time.perf_counter() - t0
+    val = pairs * per * a.steps / T
+    cb = {"value": val, "unit": UNIT, "cores": orc.num_threads(), "kind": "oracle",
+          "sample": f"{per} FP64 oracle steps of the large tank per step"}
+    print(json.dumps({"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+                      "warmup": a.warmup, "ms_per_step": 1000 * T / a.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "config": dict(desc, inner_steps_per_step=per), "impl": "reference", "cpu_baseline": cb,
+                      "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+# --------------------------------------------------------------------------
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2604_12505_gb300 import workloads as W
+    from paper_2604_12505_gb300.sph import Sim
+
+    cfg, desc = _workload(a.inner)
+    K, Wm, inner = a.steps, a.warmup, a.inner
+    sim = Sim(cfg)
+    # the fluid is spawned on a lattice and relaxed to rest with the tank held
+    # fixed before the manoeuvre (Section 5.1); untimed
+    sim.relax(a.relax, damping=2e-3)
+    xv, body = sim.state()
+    xv[:, 2:] = 0.0
+    sim.set_state(xv, body)
+    sim.check()
+    tile, tune_us = sim.autotune(steps=32)
+    total = (Wm + K) * inner
+    u_all = torch.tensor(W.bang_bang_slew(total, cfg["dt"], tau=2.0, t1=0.5), dtype=torch.float64,
+                         device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def bench_step(k):
+        return sim.step(inner, u=u_all[k * inner:(k + 1) * inner][None], record=True)
+
+    for k in range(Wm):
+        bench_step(k)
+    sim.check()
+    flush.zero_()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    c0 = sim.pair_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    torch.cuda.synchronize()
+    for k in range(K):
+        ev[k][0].record(stream)
+        bench_step(Wm + k)
+        ev[k][1].record(stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    ms = [e0.elapsed_time(e1) for e0, e1 in ev]
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    c1 = sim.pair_count()
+    sim.check()
+    T = sum(ms) / 1000.0
+    pairs = c1 - c0
+    t_red = torch.tensor([T, float(pairs)], dtype=torch.float64, device="cuda")
+    if world > 1:
+        tmax = t_red[:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        psum = t_red[1:].clone()
+        dist.all_reduce(psum, op=dist.ReduceOp.SUM)
+        T, pairs = float(tmax.item()), float(psum.item())
+    value = pairs / T
+
+    # end to end through the public API with host buffers: pinned input copy
+    # in, the step, sampled outputs copied back, every step
+    u_host = u_all.cpu().pin_memory()
+    ns = sim.samples_for(inner)
+    y_host = torch.empty((1, ns, 11), dtype=torch.float64).pin_memory()
+    h2d = inner * 3 * 8
+    d2h = ns * 11 * 8
+    e2e_ms = []
+    ce0 = sim.pair_count()
+    for k in range(K):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        u_dev = u_host[k * inner:(k + 1) * inner].to("cuda", non_blocking=True)
+        y = sim.step(inner, u=u_dev[None], record=True)
+        y_host.copy_(y, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+        flush.zero_()
+    ce1 = sim.pair_count()
+    e2e_val = (ce1 - ce0) / (sum(e2e_ms) / 1000.0)
+    if world > 1:
+        tt = torch.tensor([sum(e2e_ms) / 1000.0], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_val = (ce1 - ce0) * world / float(tt.item())
+
+    # dominant kernel: per-kernel CUDA-event durations on the launching stream
+    kt = sim.time_kernels(200)
+    sim.check()
+    cell, Wd, G, _ = sim.grid_info(0)
+    ab = algorithmic_bytes(sim.n_fluid[0], sim.n_ghost[0], G * G)
+    dom = max(kt, key=kt.get)
+    peaks, peak_src = _peaks()
+    achieved = ab[dom] / (kt[dom] * 1e-6) / 1e9
+    roof = {"bound": "hbm", "kernel": f"{dom}_kernel", "achieved": achieved, "peak": peaks["hbm_gbs"],
+            "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+            "peak_source": f"{peak_src} hbm_gbs", "kernel_us": kt, "algorithmic_bytes": ab[dom]}
+
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": Wm,
+        "ms_per_step": 1000.0 * T / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": dict(desc, parallelism="replicas" if world > 1 else "single", tile=tile,
+                       autotune_us_per_step=tune_us),
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": K * (2 * inner + 1),
+        "roofline": roof,
+        "clocks": clk,
+        "us_per_inner_step": 1e6 * T / (K * inner),
+        "pairs_per_inner_step": pairs / (K * inner * world),
+    }
+    if not a.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(cfg, a.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    sim.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -96,7 +96,9 @@ def lib():
                                   C.c_int, dp, dp]
             L.orc_grid_dims.argtypes = [P, dp, dp, ip]
             L.orc_cell_keys_f32.argtypes = [P, C.c_int, fp, C.c_int, C.c_double, C.c_double, ip]
-            L.orc_neighbor_counts_f32.argtypes = [P, C.c_int, fp, C.c_int, C.c_int, dp, dp, ip, ip, ip]
+            L.orc_neighbor_counts_f32.argtypes = [P, C.c_int, fp, C.c_int, C.c_int, dp, dp, C.c_int, ip, ip, ip, ip]
+            L.orc_pair_count.argtypes = [P, C.c_int, dp, C.c_int, dp, dp]
+            L.orc_pair_count.restype = C.c_longlong
             L.orc_num_threads.argtypes = []
             L.orc_num_threads.restype = C.c_int
             _lib = L
@@ -256,14 +258,25 @@ def cell_keys_f32(p: Params, xy_f32, anchor):
     return keys
 
 
-def neighbor_counts_f32(p: Params, xy_f32, gB, body):
+def neighbor_counts_f32(p: Params, xy_f32, gB, body, query=None):
+    """FP32 neighbour counts (n_ff, n_fg2, n_fg1) of the particles in
+    ``query`` (indices; all if None), brute force over all particles."""
     xy = np.ascontiguousarray(xy_f32, dtype=np.float32)
     gB = np.ascontiguousarray(gB, dtype=np.float64).reshape(-1, 2)
     body = np.ascontiguousarray(body, dtype=np.float64)
-    n = xy.shape[0]
+    q = None if query is None else np.ascontiguousarray(query, dtype=np.int32)
+    n = xy.shape[0] if q is None else q.shape[0]
     nff = np.zeros(n, dtype=np.int32)
     nfg2 = np.zeros(n, dtype=np.int32)
     nfg1 = np.zeros(n, dtype=np.int32)
-    lib().orc_neighbor_counts_f32(C.byref(p), n, _f(xy), xy.shape[1], gB.shape[0], _d(gB), _d(body), _i(nff),
-                                  _i(nfg2), _i(nfg1))
+    lib().orc_neighbor_counts_f32(C.byref(p), xy.shape[0], _f(xy), xy.shape[1], gB.shape[0], _d(gB), _d(body), n,
+                                  None if q is None else _i(q), _i(nff), _i(nfg2), _i(nfg1))
     return nff, nfg2, nfg1
+
+
+def pair_count(p: Params, x, gB, body) -> int:
+    """Fluid pairs r < 2h (ordered, j != i) plus fluid-ghost pairs r < h."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    gB = np.ascontiguousarray(gB, dtype=np.float64).reshape(-1, 2)
+    body = np.ascontiguousarray(body, dtype=np.float64)
+    return int(lib().orc_pair_count(C.byref(p), x.shape[0], _d(x), gB.shape[0], _d(gB), _d(body)))

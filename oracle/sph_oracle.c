@@ -544,8 +544,9 @@ int orc_shepard(const orc_params* p, int nf, const double* x, const double* rho,
  *   theta_ref  reference angle per sampling period (may be NULL); used when
  *              use_ctrl != 0 by the PD law of Eq. 28 under zero-order hold:
  *              tau_k = J w^2 (ref_k - theta_k) - 2 xi J w thetadot_k.
- *   damping    velocity damping factor per step (0 for the physical model;
- *              used only to relax a spawned fluid to rest, Section 5.1)
+ *   damping    velocity damping factor per step (0 for the physical model).
+ *              damping > 0 is the relaxation of a spawned fluid to rest
+ *              (Section 5.1): the tank is then held at its pose.
  *   y          [ceil(n_steps/outer_every), 11] outputs sampled before the
  *              step whose index is a multiple of outer_every (may be NULL):
  *              body state, fluid force/torque on the body, fluid CoM.
@@ -606,6 +607,7 @@ int orc_run(const orc_params* p, int nf, double* x, double* v, int ng, const dou
             x[2 * i] += dt * v[2 * i];
             x[2 * i + 1] += dt * v[2 * i + 1];
         }
+        if (damping > 0.0) continue; /* relaxation: the tank is held fixed */
         body[3] += dt * ba[0];
         body[4] += dt * ba[1];
         body[5] += dt * ba[2];
@@ -662,7 +664,8 @@ int orc_cell_keys_f32(const orc_params* p, int n, const float* xy, int stride, d
 }
 
 /*
- * Neighbour counts with FP32 predicates (brute force):
+ * Neighbour counts with FP32 predicates (brute force), for the particles
+ * listed in qidx[nq] (all particles if qidx is NULL):
  *   n_ff[i]   #{ j != i : fma(dx, dx, dy*dy) < fl32((2h)^2) },  dx = x_i - x_j
  *   n_fg2[i]  #{ g : same with (2h)^2 }  (ghosts entering Eq. 14)
  *   n_fg1[i]  #{ g : same with h^2 }     (ghosts entering Eqs. 16 and 18)
@@ -670,7 +673,8 @@ int orc_cell_keys_f32(const orc_params* p, int n, const float* xy, int stride, d
  * r_g from Eq. 21 in FP64.
  */
 int orc_neighbor_counts_f32(const orc_params* p, int nf, const float* xy, int stride, int ng, const double* gB,
-                            const double* body, int32_t* n_ff, int32_t* n_fg2, int32_t* n_fg1)
+                            const double* body, int nq, const int32_t* qidx, int32_t* n_ff, int32_t* n_fg2,
+                            int32_t* n_fg1)
 {
     double h = orc_h(p);
     float R2 = (float)((2.0 * h) * (2.0 * h));
@@ -678,7 +682,9 @@ int orc_neighbor_counts_f32(const orc_params* p, int nf, const float* xy, int st
     double* gw = (double*)malloc(sizeof(double) * 2 * (ng > 0 ? ng : 1));
     if (!gw) return -1;
     orc_ghost_world(ng, gB, body, gw, NULL, NULL);
-    for (int i = 0; i < nf; ++i) {
+    if (!qidx) nq = nf;
+    for (int q = 0; q < nq; ++q) {
+        int i = qidx ? qidx[q] : q;
         float xi = xy[(size_t)stride * i], yi = xy[(size_t)stride * i + 1];
         int c = 0;
         for (int j = 0; j < nf; ++j) {
@@ -688,7 +694,7 @@ int orc_neighbor_counts_f32(const orc_params* p, int nf, const float* xy, int st
             float r2 = fmaf(ddx, ddx, ddy * ddy);
             c += r2 < R2;
         }
-        n_ff[i] = c;
+        n_ff[q] = c;
         int c2 = 0, c1 = 0;
         for (int g = 0; g < ng; ++g) {
             float hx = (float)gw[2 * g], hy = (float)gw[2 * g + 1];
@@ -699,9 +705,38 @@ int orc_neighbor_counts_f32(const orc_params* p, int nf, const float* xy, int st
             c2 += r2 < R2;
             c1 += r2 < h2;
         }
-        n_fg2[i] = c2;
-        n_fg1[i] = c1;
+        n_fg2[q] = c2;
+        n_fg1[q] = c1;
     }
     free(gw);
     return 0;
+}
+
+/*
+ * Pair interactions of one evaluation of Algorithm 1 (FP64 predicates):
+ * ordered fluid pairs j != i with r < 2h (Eqs. 10, 12) plus fluid-ghost pairs
+ * with r < h (Eqs. 16, 18).
+ */
+long long orc_pair_count(const orc_params* p, int nf, const double* x, int ng, const double* gB, const double* body)
+{
+    const double h = orc_h(p);
+    double* gw = (double*)malloc(sizeof(double) * 2 * (ng > 0 ? ng : 1));
+    int* nb = (int*)malloc(sizeof(int) * (nf + ng + 1));
+    if (!gw || !nb) {
+        free(gw), free(nb);
+        return -1;
+    }
+    orc_ghost_world(ng, gB, body, gw, NULL, NULL);
+    bucket_t bf, bg;
+    if (bucket_build(&bf, nf, x, 2.0 * h) || bucket_build(&bg, ng, gw, 2.0 * h)) return -1;
+    long long total = 0;
+    for (int i = 0; i < nf; ++i) {
+        int c = bucket_query(&bf, x, x[2 * i], x[2 * i + 1], 2.0 * h, nb);
+        total += c - 1; /* the particle itself is in its own list */
+        total += bucket_query(&bg, gw, x[2 * i], x[2 * i + 1], h, nb);
+    }
+    bucket_free(&bf);
+    bucket_free(&bg);
+    free(gw), free(nb);
+    return total;
 }

@@ -1,0 +1,717 @@
+// sph_api.cu -- host implementation of the C ABI declared in include/sph.h.
+//
+// Tank construction (Section 3.2 geometry, done once per handle on the host),
+// device allocation, graph-captured step chains and state transfer.  Every
+// per-step computation runs in the kernels of sph_kernels.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstddef>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sph.h"
+#include "sph_common.cuh"
+#include "sph_launch.h"
+
+using namespace sph;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) return fail(SPH_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kGraphSteps = 32;
+
+struct TankHost {
+    sph_params p;
+    std::vector<double> xf;   // [n_f, 2] builder order
+    std::vector<double> gB;   // [n_g, 2] builder order
+    int n_f = 0, n_g = 0, G = 0;
+    double h = 0, cell = 0, W = 0;
+};
+
+// Area of the part of the disk |p| <= R below the chord y = c.
+double segment_area(double R, double c)
+{
+    if (c <= -R) return 0.0;
+    if (c >= R) return kPi * R * R;
+    return R * R * (kPi - std::acos(c / R)) + c * std::sqrt(R * R - c * c);
+}
+
+double chord_for_fill(double R, double fill)
+{
+    double lo = -R, hi = R, want = fill * kPi * R * R;
+    for (int i = 0; i < 200; ++i) {
+        double mid = 0.5 * (lo + hi);
+        (segment_area(R, mid) < want ? lo : hi) = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+int validate(const sph_params& p)
+{
+    if (!(p.R > 0) || !(p.dx > 0) || !(p.dx < p.R) || !(p.fill >= 0 && p.fill <= 1) || !(p.h_over_dx > 0) ||
+        p.n_rings < 1 || p.outer_every < 1 || !(p.rho0 > 0) || !(p.m_body > 0) || !(p.J_body > 0) || !(p.dt > 0))
+        return fail(SPH_E_INVAL, "invalid sph_params");
+    return SPH_OK;
+}
+
+// Fluid lattice and ghost rings of one tank (geometry stated on sph_params).
+void build_tank(TankHost& t)
+{
+    const sph_params& p = t.p;
+    const double c = chord_for_fill(p.R, p.fill), rin = p.R - 0.5 * p.dx;
+    const int L = (int)std::ceil(p.R / p.dx) + 2;
+    for (int j = -L; j <= L; ++j)
+        for (int i = -L; i <= L; ++i) {
+            double x = ((double)i + 0.5) * p.dx, y = ((double)j + 0.5) * p.dx;
+            if (x * x + y * y <= rin * rin && y <= c) {
+                t.xf.push_back(x);
+                t.xf.push_back(y);
+            }
+        }
+    for (int k = 0; k < p.n_rings; ++k) {
+        const double rk = p.R + ((double)k + 0.5) * p.dx;
+        const int nk = (int)std::round(2.0 * kPi * rk / p.dx);
+        for (int j = 0; j < nk; ++j) {
+            const double phi = 2.0 * kPi * (double)j / (double)nk;
+            t.gB.push_back(rk * std::cos(phi));
+            t.gB.push_back(rk * std::sin(phi));
+        }
+    }
+    t.n_f = (int)t.xf.size() / 2;
+    t.n_g = (int)t.gB.size() / 2;
+    t.h = p.h_over_dx * p.dx;
+    t.cell = 2.0 * t.h * (1.0 + 1.0 / 1024.0);
+    t.W = p.R + ((double)p.n_rings + 1.0) * p.dx + 2.0 * t.cell;
+    t.G = (int)std::ceil(2.0 * t.W / t.cell);
+}
+
+template <class T>
+int dalloc(T** p, size_t n)
+{
+    *p = nullptr;
+    if (n == 0) n = 1;
+    cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+    if (e != cudaSuccess) return fail(SPH_E_NOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return SPH_OK;
+}
+
+}  // namespace
+
+struct sph_sim {
+    int B = 0;
+    std::vector<TankHost> tanks;
+    int n_f_total = 0, n_g_total = 0, n_cells_total = 0;
+    int tile_code = 3;
+    int n_tiles[SPH_TILE_COUNT + 1] = {0};
+    SimDev S{};
+    // owned device buffers
+    TankDev* d_tank = nullptr;
+    BodyDev* d_body = nullptr;
+    RunDev* d_run = nullptr;
+    int4* d_tiles[SPH_TILE_COUNT + 1] = {nullptr};
+    int* d_tile_first[SPH_TILE_COUNT + 1] = {nullptr};
+    int* d_part_tank = nullptr;
+    double* d_scratch_body = nullptr;
+    float* d_scratch_xv = nullptr;
+    long long host_step = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    int graph_tile = 0;
+    bool use_pdl = true;
+
+    SimDev dev() const
+    {
+        SimDev s = S;
+        s.tiles = d_tiles[tile_code];
+        s.tile_tank_first = d_tile_first[tile_code];
+        s.n_tiles = n_tiles[tile_code];
+        return s;
+    }
+
+    int step_launch(const EvalOut& E, int eval, cudaStream_t st)
+    {
+        cudaError_t e = launch_step(dev(), E, eval, tile_code, n_tiles[tile_code], st, use_pdl && !eval);
+        if (e != cudaSuccess) return fail(SPH_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
+        return SPH_OK;
+    }
+};
+
+namespace {
+
+void free_sim(sph_sim* s)
+{
+    if (!s) return;
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    cudaFree(s->d_tank);
+    cudaFree(s->d_body);
+    cudaFree(s->d_run);
+    for (int c = 0; c <= SPH_TILE_COUNT; ++c) {
+        cudaFree(s->d_tiles[c]);
+        cudaFree(s->d_tile_first[c]);
+    }
+    cudaFree(s->d_part_tank);
+    cudaFree(s->d_scratch_body);
+    cudaFree(s->d_scratch_xv);
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(s->S.pv[b]);
+        cudaFree(s->S.pid[b]);
+        cudaFree(s->S.count[b]);
+    }
+    cudaFree(s->S.rhoP);
+    cudaFree(s->S.partials);
+    cudaFree((void*)s->S.gB);
+    cudaFree((void*)s->S.gstart);
+    cudaFree(s->S.gpos);
+    cudaFree(s->S.gvel);
+    delete s;
+}
+
+TankDev make_tank_dev(const TankHost& t)
+{
+    const sph_params& p = t.p;
+    TankDev d{};
+    const double h = t.h;
+    const double sigma = p.sigma_cubic > 0 ? p.sigma_cubic : 5.0 / (14.0 * kPi);
+    d.h = (float)h;
+    d.inv_h = (float)(1.0 / h);
+    d.R2 = (float)((2.0 * h) * (2.0 * h));
+    d.h2 = (float)(h * h);
+    d.cW = (float)(sigma / (h * h));
+    d.cdW = (float)(sigma / (h * h * h));
+    d.cS = (float)(10.0 / (kPi * std::pow(h, 5)));
+    d.cdS = (float)(-30.0 / (kPi * std::pow(h, 5)));
+    const double m = p.rho0 * p.dx * p.dx;
+    d.m = (float)m;
+    d.inv_m = (float)(1.0 / m);
+    d.k = (float)p.k;
+    d.rho0 = (float)p.rho0;
+    d.gamma1 = (float)p.gamma1;
+    d.visc_a = (float)(2.0 * p.alpha * h);
+    d.beta2 = (float)(2.0 * p.beta);
+    d.epsh2 = (float)(p.eps * h * h);
+    d.dt = (float)p.dt;
+    d.gp_sign = (float)p.ghost_pressure_sign;
+    d.grav_x = (float)p.grav_x;
+    d.grav_y = (float)p.grav_y;
+    d.inv_cell = (float)(1.0 / t.cell);
+    d.g_orig = (float)(-t.W);
+    d.g_inv_cell = (float)(1.0 / t.cell);
+    double rmin = 1e300;
+    for (int g = 0; g < t.n_g; ++g) rmin = std::min(rmin, std::hypot(t.gB[2 * g], t.gB[2 * g + 1]));
+    const double rin = rmin - t.cell * 1.01;
+    d.ghost_rin2 = rin > 0 ? (float)(rin * rin) : -1.0f;
+    d.G = t.G;
+    d.n_f = t.n_f;
+    d.n_g = t.n_g;
+    d.outer_every = p.outer_every;
+    d.W = t.W;
+    d.cell = t.cell;
+    d.m_body = p.m_body;
+    d.J_body = p.J_body;
+    d.dt_d = p.dt;
+    d.grav_xd = p.grav_x;
+    d.grav_yd = p.grav_y;
+    return d;
+}
+
+int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
+{
+    if (!p || !out || B < 1) return fail(SPH_E_INVAL, "sph_create: NULL argument or B < 1");
+    *out = nullptr;
+    for (int b = 0; b < B; ++b)
+        if (validate(p[b])) return SPH_E_INVAL;
+    sph_sim* s = new sph_sim();
+    s->B = B;
+    s->tanks.resize(B);
+    std::vector<TankDev> td(B);
+    std::vector<float> xv;
+    std::vector<int> part_tank;
+    std::vector<float4> gB_sorted;
+    std::vector<int> gstart;
+    int cell_base = 0, ghost_base = 0, gcell_base = 0, pid_base = 0;
+    for (int b = 0; b < B; ++b) {
+        TankHost& t = s->tanks[b];
+        t.p = p[b];
+        build_tank(t);
+        if (t.G > 4096) {
+            free_sim(s);
+            return fail(SPH_E_UNSUPPORTED, "sph_create: grid wider than 4096 cells (dx too small for R)");
+        }
+        td[b] = make_tank_dev(t);
+        td[b].cell_base = cell_base;
+        td[b].ghost_base = ghost_base;
+        td[b].gcell_base = gcell_base;
+        td[b].pid_base = pid_base;
+        // ghosts sorted by body-frame cell (stable), cell table with global indices
+        const int G = t.G;
+        std::vector<int> key(t.n_g), order(t.n_g);
+        for (int g = 0; g < t.n_g; ++g) {
+            int cx = (int)std::floor((t.gB[2 * g] + t.W) / t.cell), cy = (int)std::floor((t.gB[2 * g + 1] + t.W) / t.cell);
+            cx = std::min(std::max(cx, 0), G - 1);
+            cy = std::min(std::max(cy, 0), G - 1);
+            key[g] = cy * G + cx;
+            order[g] = g;
+        }
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return key[a] < key[c]; });
+        std::vector<int> cnt((size_t)G * G + 1, 0);
+        for (int g = 0; g < t.n_g; ++g) cnt[key[g] + 1]++;
+        for (size_t c = 0; c < (size_t)G * G; ++c) cnt[c + 1] += cnt[c];
+        for (size_t c = 0; c <= (size_t)G * G; ++c) gstart.push_back(ghost_base + cnt[c]);
+        for (int q = 0; q < t.n_g; ++q) {
+            int g = order[q];
+            const float2 bx = df_split(t.gB[2 * g]), by = df_split(t.gB[2 * g + 1]);
+            gB_sorted.push_back(make_float4(bx.x, bx.y, by.x, by.y));
+        }
+        for (int i = 0; i < t.n_f; ++i) {
+            xv.push_back((float)t.xf[2 * i]);
+            xv.push_back((float)t.xf[2 * i + 1]);
+            xv.push_back(0.f);
+            xv.push_back(0.f);
+            part_tank.push_back(b);
+        }
+        cell_base += G * G;
+        ghost_base += t.n_g;
+        gcell_base += G * G + 1;
+        pid_base += t.n_f;
+    }
+    s->n_f_total = pid_base;
+    s->n_g_total = ghost_base;
+    s->n_cells_total = cell_base;
+    if ((long long)cell_base * kCap > (1ll << 31) - 1) {
+        free_sim(s);
+        return fail(SPH_E_UNSUPPORTED, "sph_create: more than 2^31 grid slots");
+    }
+    // tile tables for every shape
+    int max_tiles = 0;
+    std::vector<std::vector<int4>> tiles(SPH_TILE_COUNT + 1);
+    std::vector<std::vector<int>> first(SPH_TILE_COUNT + 1);
+    for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
+        int TX, TY;
+        tile_dims(code, &TX, &TY);
+        for (int b = 0; b < B; ++b) {
+            first[code].push_back((int)tiles[code].size());
+            const int G = s->tanks[b].G;
+            int local = 0;
+            for (int ty = 0; ty < G; ty += TY)
+                for (int tx = 0; tx < G; tx += TX) tiles[code].push_back(make_int4(b, tx, ty, local++));
+        }
+        first[code].push_back((int)tiles[code].size());
+        s->n_tiles[code] = (int)tiles[code].size();
+        max_tiles = std::max(max_tiles, s->n_tiles[code]);
+    }
+    s->tile_code = 3;
+
+    int rc = SPH_OK;
+    const size_t nslot = (size_t)s->n_cells_total * kCap;
+    rc |= dalloc(&s->d_tank, B);
+    rc |= dalloc(&s->d_body, B);
+    rc |= dalloc(&s->d_run, 1);
+    for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
+        rc |= dalloc(&s->d_tiles[code], tiles[code].size());
+        rc |= dalloc(&s->d_tile_first[code], first[code].size());
+    }
+    rc |= dalloc(&s->d_part_tank, s->n_f_total);
+    rc |= dalloc(&s->d_scratch_body, 6 * (size_t)B);
+    rc |= dalloc(&s->d_scratch_xv, 4 * (size_t)s->n_f_total);
+    for (int b = 0; b < 2; ++b) {
+        rc |= dalloc(&s->S.pv[b], nslot);
+        rc |= dalloc(&s->S.pid[b], nslot);
+        rc |= dalloc(&s->S.count[b], s->n_cells_total);
+    }
+    rc |= dalloc(&s->S.rhoP, nslot);
+    rc |= dalloc(&s->S.partials, max_tiles);
+    float4* gB_d;
+    int* gstart_d;
+    rc |= dalloc(&gB_d, gB_sorted.size());
+    rc |= dalloc(&gstart_d, gstart.size());
+    s->S.gB = gB_d;
+    s->S.gstart = gstart_d;
+    rc |= dalloc(&s->S.gpos, s->n_g_total);
+    rc |= dalloc(&s->S.gvel, s->n_g_total);
+    if (rc) {
+        std::string msg = g_err;
+        free_sim(s);
+        return fail(SPH_E_NOMEM, msg);
+    }
+    s->S.tank = s->d_tank;
+    s->S.body = s->d_body;
+    s->S.run = s->d_run;
+    s->S.B = B;
+
+#define CKF(call)                                                                                 \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            free_sim(s);                                                                          \
+            return fail(SPH_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_));            \
+        }                                                                                         \
+    } while (0)
+    CKF(cudaMemcpy(s->d_tank, td.data(), B * sizeof(TankDev), cudaMemcpyHostToDevice));
+    CKF(cudaMemset(s->d_body, 0, B * sizeof(BodyDev)));
+    CKF(cudaMemset(s->d_run, 0, sizeof(RunDev)));
+    for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
+        CKF(cudaMemcpy(s->d_tiles[code], tiles[code].data(), tiles[code].size() * sizeof(int4), cudaMemcpyHostToDevice));
+        CKF(cudaMemcpy(s->d_tile_first[code], first[code].data(), first[code].size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
+    CKF(cudaMemcpy(s->d_part_tank, part_tank.data(), part_tank.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!gB_sorted.empty()) {
+        CKF(cudaMemcpy(gB_d, gB_sorted.data(), gB_sorted.size() * sizeof(float4), cudaMemcpyHostToDevice));
+    }
+    CKF(cudaMemcpy(gstart_d, gstart.data(), gstart.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CKF(cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking));
+    // initial state: fluid at rest on the lattice, body at the origin at rest
+    std::vector<double> body0(6 * (size_t)B, 0.0);
+    CKF(cudaMemcpy(s->d_scratch_xv, xv.data(), xv.size() * sizeof(float), cudaMemcpyHostToDevice));
+    CKF(cudaMemcpy(s->d_scratch_body, body0.data(), body0.size() * sizeof(double), cudaMemcpyHostToDevice));
+#undef CKF
+    *out = s;
+    int r2 = sph_set_state(s, s->d_scratch_xv, s->d_scratch_body, st);
+    if (r2 == SPH_OK && cudaStreamSynchronize(st) != cudaSuccess) r2 = fail(SPH_E_CUDA, "sph_create: initial binning failed");
+    if (r2 != SPH_OK) {
+        free_sim(s);
+        *out = nullptr;
+    }
+    return r2;
+}
+
+int ensure_graph(sph_sim* s)
+{
+    if (s->graph && s->graph_tile == s->tile_code) return SPH_OK;
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    cudaGraph_t g;
+    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
+    EvalOut E{};
+    for (int i = 0; i < kGraphSteps; ++i) {
+        int rc = s->step_launch(E, 0, s->cap);
+        if (rc) {
+            cudaStreamEndCapture(s->cap, &g);
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+    }
+    CK(cudaStreamEndCapture(s->cap, &g));
+    cudaError_t e = cudaGraphInstantiate(&s->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(SPH_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    s->graph_tile = s->tile_code;
+    return SPH_OK;
+}
+
+long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
+
+}  // namespace
+
+extern "C" {
+
+const char* sph_last_error(void) { return g_err.c_str(); }
+
+int sph_create(const sph_params* p, void* stream, sph_sim** out) { return create_impl(p, 1, (cudaStream_t)stream, out); }
+
+int sph_create_batch(const sph_params* p, int32_t B, void* stream, sph_sim** out)
+{
+    return create_impl(p, B, (cudaStream_t)stream, out);
+}
+
+int sph_destroy(sph_sim* sim)
+{
+    if (!sim) return SPH_OK;
+    cudaDeviceSynchronize();
+    free_sim(sim);
+    return SPH_OK;
+}
+
+int sph_counts(const sph_sim* sim, int32_t* B, int32_t* n_fluid, int32_t* n_ghost)
+{
+    if (!sim) return fail(SPH_E_INVAL, "sph_counts: NULL handle");
+    if (B) *B = sim->B;
+    for (int b = 0; b < sim->B; ++b) {
+        if (n_fluid) n_fluid[b] = sim->tanks[b].n_f;
+        if (n_ghost) n_ghost[b] = sim->tanks[b].n_g;
+    }
+    return SPH_OK;
+}
+
+int sph_ghosts_body(const sph_sim* sim, int32_t b, double* gB_host)
+{
+    if (!sim || !gB_host || b < 0 || b >= sim->B) return fail(SPH_E_INVAL, "sph_ghosts_body: bad argument");
+    std::memcpy(gB_host, sim->tanks[b].gB.data(), sim->tanks[b].gB.size() * sizeof(double));
+    return SPH_OK;
+}
+
+int sph_get_state(sph_sim* sim, float* xv, double* body, void* stream)
+{
+    if (!sim) return fail(SPH_E_INVAL, "sph_get_state: NULL handle");
+    const int buf = (int)(sim->host_step & 1);
+    CK(launch_get_state(sim->S, xv, body, sim->n_cells_total, buf, (cudaStream_t)stream));
+    return SPH_OK;
+}
+
+int sph_set_state(sph_sim* sim, const float* xv, const double* body, void* stream)
+{
+    if (!sim || !xv || !body) return fail(SPH_E_INVAL, "sph_set_state: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int buf = (int)(sim->host_step & 1);
+    CK(cudaMemsetAsync(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int), st));
+    CK(launch_set_body(sim->S, body, buf, st));
+    CK(launch_bin_flat(sim->S, xv, sim->d_part_tank, sim->n_f_total, buf, st));
+    return SPH_OK;
+}
+
+int sph_samples_for(const sph_sim* sim, int32_t n_steps, int32_t* n_samples)
+{
+    if (!sim || !n_samples || n_steps < 0) return fail(SPH_E_INVAL, "sph_samples_for: bad argument");
+    // all tanks of a batch share outer_every only if equal; samples are counted per tank 0
+    const long long oe = sim->tanks[0].p.outer_every;
+    const long long s0 = sim->host_step, s1 = sim->host_step + n_steps;
+    *n_samples = (int32_t)(ceil_div(s1, oe) - ceil_div(s0, oe));
+    return SPH_OK;
+}
+
+int sph_step(sph_sim* sim, const double* u, int32_t n_steps, const sph_ctrl* pd, double* y_out, void* stream)
+{
+    if (!sim || n_steps < 0) return fail(SPH_E_INVAL, "sph_step: bad argument");
+    if (n_steps == 0) return SPH_OK;
+    for (int b = 1; b < sim->B; ++b)
+        if (sim->tanks[b].p.outer_every != sim->tanks[0].p.outer_every)
+            return fail(SPH_E_UNSUPPORTED, "sph_step: tanks of a batch must share outer_every");
+    cudaStream_t st = (cudaStream_t)stream;
+    int32_t ns = 0;
+    sph_samples_for(sim, n_steps, &ns);
+    RunDev d{};
+    d.u = u;
+    d.u_tank_stride = 3ll * n_steps;
+    d.y = y_out;
+    d.y_tank_stride = (long long)ns * SPH_NY;
+    if (pd && pd->enabled) {
+        d.ctrl_on = 1;
+        d.ctrl_J = pd->J;
+        d.ctrl_w = pd->omega;
+        d.ctrl_xi = pd->xi;
+        d.theta_ref = pd->theta_ref;
+        d.ref_stride = pd->ref_stride;
+    }
+    CK(launch_set_run(sim->d_run, d, st));
+    int rc = ensure_graph(sim);
+    if (rc) return rc;
+    int left = n_steps;
+    EvalOut E{};
+    while (left >= kGraphSteps) {
+        CK(cudaGraphLaunch(sim->graph, st));
+        left -= kGraphSteps;
+    }
+    for (; left > 0; --left) {
+        rc = sim->step_launch(E, 0, st);
+        if (rc) return rc;
+    }
+    sim->host_step += n_steps;
+    return SPH_OK;
+}
+
+int sph_relax(sph_sim* sim, int32_t n_steps, double damping, void* stream)
+{
+    if (!sim || n_steps < 0 || !(damping >= 0.0 && damping < 1.0)) return fail(SPH_E_INVAL, "sph_relax: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    RunDev d{};
+    d.damping = (float)damping;
+    d.body_fixed = 1;
+    CK(launch_set_run(sim->d_run, d, st));
+    EvalOut E{};
+    for (int i = 0; i < n_steps; ++i) {
+        int rc = sim->step_launch(E, 0, st);
+        if (rc) return rc;
+    }
+    sim->host_step += n_steps;
+    return SPH_OK;
+}
+
+int sph_eval(sph_sim* sim, const double* u, float* rho, float* drho, float* acc, int32_t* nbr, int32_t* keys,
+             double* body_out, void* stream)
+{
+    if (!sim) return fail(SPH_E_INVAL, "sph_eval: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    RunDev d{};
+    d.u = u;
+    d.u_tank_stride = 3;
+    CK(launch_set_run(sim->d_run, d, st));
+    EvalOut E{rho, drho, acc, nbr, keys, body_out};
+    return sim->step_launch(E, 1, st);
+}
+
+int sph_grid_info(sph_sim* sim, int32_t b, double* cell, double* half_width, int32_t* G, double* anchor_xy)
+{
+    if (!sim || b < 0 || b >= sim->B) return fail(SPH_E_INVAL, "sph_grid_info: bad argument");
+    CK(cudaDeviceSynchronize());
+    const TankHost& t = sim->tanks[b];
+    if (cell) *cell = t.cell;
+    if (half_width) *half_width = t.W;
+    if (G) *G = t.G;
+    if (anchor_xy) {
+        BodyDev bd;
+        CK(cudaMemcpy(&bd, sim->d_body + b, sizeof(BodyDev), cudaMemcpyDeviceToHost));
+        const int buf = (int)(sim->host_step & 1);
+        anchor_xy[0] = bd.anchor[buf][0];
+        anchor_xy[1] = bd.anchor[buf][1];
+    }
+    return SPH_OK;
+}
+
+int sph_check(sph_sim* sim, int32_t* flags, int32_t reset, void* stream)
+{
+    if (!sim) return fail(SPH_E_INVAL, "sph_check: NULL handle");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<BodyDev> bd(sim->B);
+    CK(cudaMemcpy(bd.data(), sim->d_body, sim->B * sizeof(BodyDev), cudaMemcpyDeviceToHost));
+    int f = 0;
+    for (auto& b : bd) f |= b.flags;
+    if (flags) *flags = f;
+    if (reset && f) {
+        for (int b = 0; b < sim->B; ++b)
+            CK(cudaMemset((char*)(sim->d_body + b) + offsetof(BodyDev, flags), 0, sizeof(int)));
+        CK(cudaDeviceSynchronize());
+    }
+    if (f & ~SPH_FLAG_TIMEOUT) return fail(SPH_E_DIVERGED, "health check tripped: flags " + std::to_string(f));
+    if (f) return fail(SPH_E_TIMEOUT, "a bounded device-side wait gave up");
+    return SPH_OK;
+}
+
+int sph_pair_count(sph_sim* sim, int64_t* pairs, void* stream)
+{
+    if (!sim || !pairs) return fail(SPH_E_INVAL, "sph_pair_count: bad argument");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    std::vector<BodyDev> bd(sim->B);
+    CK(cudaMemcpy(bd.data(), sim->d_body, sim->B * sizeof(BodyDev), cudaMemcpyDeviceToHost));
+    unsigned long long t = 0;
+    for (auto& b : bd) t += b.pairs;
+    *pairs = (int64_t)t;
+    return SPH_OK;
+}
+
+int sph_set_tile(sph_sim* sim, int32_t tile)
+{
+    if (!sim || tile < 0 || tile > SPH_TILE_COUNT) return fail(SPH_E_INVAL, "sph_set_tile: bad tile code");
+    sim->tile_code = tile == 0 ? 3 : tile;
+    return SPH_OK;
+}
+
+int sph_autotune(sph_sim* sim, int32_t steps, int32_t* chosen, double* us_per_step, void* stream)
+{
+    if (!sim || steps < 1) return fail(SPH_E_INVAL, "sph_autotune: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    // snapshot: particles in index order, raw body records and run record
+    std::vector<BodyDev> body(sim->B);
+    RunDev run;
+    CK(cudaStreamSynchronize(st));
+    CK(cudaMemcpy(body.data(), sim->d_body, sim->B * sizeof(BodyDev), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&run, sim->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost));
+    int rc = sph_get_state(sim, sim->d_scratch_xv, nullptr, st);
+    if (rc) return rc;
+    const long long step0 = sim->host_step;
+    const int old_tile = sim->tile_code;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int best = old_tile;
+    float best_ms = 1e30f;
+    for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
+        sim->tile_code = code;
+        rc = sph_step(sim, nullptr, 2, nullptr, nullptr, stream);
+        if (rc) break;
+        CK(cudaEventRecord(e0, st));
+        rc = sph_step(sim, nullptr, steps, nullptr, nullptr, stream);
+        if (rc) break;
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (us_per_step) us_per_step[code - 1] = 1000.0 * ms / steps;
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = code;
+        }
+        // restore the snapshot exactly (same anchors, same grid membership)
+        sim->host_step = step0;
+        CK(cudaMemcpy(sim->d_body, body.data(), sim->B * sizeof(BodyDev), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(sim->d_run, &run, sizeof(RunDev), cudaMemcpyHostToDevice));
+        const int buf = (int)(step0 & 1);
+        CK(cudaMemset(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int)));
+        CK(launch_bin_flat(sim->S, sim->d_scratch_xv, sim->d_part_tank, sim->n_f_total, buf, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        sim->tile_code = old_tile;
+        return rc;
+    }
+    sim->tile_code = best;
+    if (chosen) *chosen = best;
+    return SPH_OK;
+}
+
+int sph_time_kernels(sph_sim* sim, int32_t n_steps, double* us, void* stream)
+{
+    if (!sim || n_steps < 1 || !us) return fail(SPH_E_INVAL, "sph_time_kernels: bad argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    RunDev d{};
+    CK(launch_set_run(sim->d_run, d, st));
+    cudaEvent_t ev[3];
+    for (auto& e : ev) CK(cudaEventCreate(&e));
+    double acc[2] = {0.0, 0.0};
+    const SimDev S = sim->dev();
+    EvalOut E{};
+    for (int i = 0; i < n_steps; ++i) {
+        for (int ph = 0; ph < 2; ++ph) {
+            CK(cudaEventRecord(ev[ph], st));
+            CK(launch_phase(S, E, 0, sim->tile_code, sim->n_tiles[sim->tile_code], ph, st, false));
+        }
+        CK(cudaEventRecord(ev[2], st));
+        CK(cudaEventSynchronize(ev[2]));
+        for (int ph = 0; ph < 2; ++ph) {
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
+            acc[ph] += ms;
+        }
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    for (int ph = 0; ph < 2; ++ph) us[ph] = 1000.0 * acc[ph] / n_steps;
+    sim->host_step += n_steps;
+    return SPH_OK;
+}
+
+int sph_run_batch(const sph_params* p, int32_t B, const double* u_profiles, int32_t T, const sph_ctrl* pd,
+                  double* y_out, int32_t* n_particles_out, void* stream)
+{
+    if (!p || B < 1 || T < 0) return fail(SPH_E_INVAL, "sph_run_batch: bad argument");
+    sph_sim* s = nullptr;
+    int rc = sph_create_batch(p, B, stream, &s);
+    if (rc) return rc;
+    if (n_particles_out) sph_counts(s, nullptr, n_particles_out, nullptr);
+    rc = sph_step(s, u_profiles, T, pd, y_out, stream);
+    if (rc == SPH_OK) rc = sph_check(s, nullptr, 0, stream);
+    sph_destroy(s);
+    return rc;
+}
+
+}  // extern "C"

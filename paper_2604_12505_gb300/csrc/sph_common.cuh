@@ -1,0 +1,208 @@
+// sph_common.cuh -- device-side data layout and SPH arithmetic shared by the
+// CUDA translation units of the simulator (not part of the C ABI).
+//
+// Layout in device memory (all tanks of a batch concatenated):
+//   * neighbour grid, double-buffered by step parity: per cell a count and
+//     SPH_CELL_CAPACITY slots; a slot holds float4 (x, y, vx, vy) and the
+//     particle's global index.  The fluid state lives only in these slots:
+//     the force kernel integrates a particle and writes it straight into its
+//     cell of the other buffer (atomic slot claim), so no sort or scan pass
+//     exists.  Within a cell the kernels order particles by index, which
+//     makes every neighbour sum deterministic.
+//   * per-slot float2 (rho, P / rho^2) written by the density kernel.
+//   * ghosts: body-frame positions (two-float) binned once into a body-frame
+//     grid, and per step the world position as an FP32 (hi, lo) pair plus
+//     FP32 velocity and lever arm (Eq. 21), written by the density pass for
+//     every ghost it visits and read by the force pass.
+//   * per tank: FP32/FP64 constants (TankDev), FP64 body state (BodyDev).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+constexpr int kCap = SPH_CELL_CAPACITY;
+
+struct TankDev {
+    // FP32 constants of the kernels
+    float h, inv_h, R2, h2;       // smoothing length, 1/h, fl32((2h)^2), fl32(h^2)
+    float cW, cdW;                // sigma/h^2, sigma/h^3 (Eq. 22)
+    float cS, cdS;                // 10/(pi h^5), -30/(pi h^5) (Eq. 23)
+    float m, inv_m, k, rho0;      // particle mass, EOS (Eq. 11)
+    float gamma1, visc_a, beta2, epsh2;  // gamma1, 2 alpha h, 2 beta, eps h^2
+    float dt, gp_sign, grav_x, grav_y;
+    float inv_cell;               // fl32(1/s)
+    float g_orig, g_inv_cell;     // body-frame ghost grid origin (-W) and 1/s, FP32
+    float ghost_rin2;             // particles with |xi|^2 below this see no ghost
+    int G;                        // cells per side (fluid and ghost grid)
+    int n_f, n_g;
+    int cell_base;                // first cell of this tank in the global grid arrays
+    int ghost_base;               // first ghost of this tank
+    int gcell_base;               // first entry of this tank's ghost-cell table
+    int pid_base;                 // first global particle index of this tank
+    int outer_every;
+    double W, cell;               // grid half-width and cell side (FP64)
+    double m_body, J_body, dt_d;
+    double grav_xd, grav_yd;
+};
+
+struct BodyDev {
+    double r[2], th, v[2], w;     // r, theta, rdot, thetadot at the current step
+    double c, s;                  // cos(theta), sin(theta)
+    double anchor[2][2];          // FP64 anchor of grid buffer 0 / 1
+    double tau_c;                 // controller torque held by the zero-order hold
+    unsigned long long pairs;     // cumulative pair interactions
+    // FP32 forms written once per step by the body update, so that no CTA
+    // converts FP64 (the FP64 pipe of this GPU is narrow):
+    float fc, fs, frx, fry;       // cos, sin, r rounded -- only used to select ghost cells
+    float fo_next[2];             // fl32(r - W): origin of the grid the force pass bins into
+    float2 dc, ds, drx, dry;      // cos, sin, r as two-float (hi, lo) splits of the FP64 values
+    float fvx, fvy, fw;           // rdot, thetadot rounded to FP32
+    unsigned int done;            // tiles of this tank finished in the current force pass
+    int flags;                    // SPH_FLAG_* bits
+};
+
+// Two-float (hi + lo) arithmetic on the FP32 pipe (error-free transformations,
+// about 48 significant bits): used for ghost world positions (Eq. 21).
+__host__ __device__ __forceinline__ float2 df_split(double v)
+{
+    const float hi = (float)v;
+    return make_float2(hi, (float)(v - (double)hi));
+}
+
+__device__ __forceinline__ float2 df_norm(float s, float e)
+{
+    const float hi = s + e;
+    return make_float2(hi, e - (hi - s));
+}
+
+__device__ __forceinline__ float2 df_add(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb) + a.y + b.y;
+    return df_norm(s, e);
+}
+
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b)
+{
+    const float p = a.x * b.x;
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, e);
+    e = fmaf(a.y, b.x, e);
+    return df_norm(p, e);
+}
+
+struct RunDev {
+    long long step;               // global inner-step counter
+    long long step0;              // step counter at the start of the current call
+    const double* u;              // [B, n_rows, 3] inputs (NULL: zero)
+    long long u_tank_stride;      // doubles between tanks in u
+    double* y;                    // [B, n_samples, SPH_NY] samples (NULL: none)
+    long long y_tank_stride;
+    const double* theta_ref;      // [B, n_samples] (NULL: 0)
+    long long ref_stride;
+    double ctrl_J, ctrl_w, ctrl_xi;
+    int ctrl_on;
+    float damping;                // relaxation: v <- (1 - damping) v after the kick (0: physical model)
+    int body_fixed;               // relaxation: the tank is held at its pose
+    unsigned int tanks_done;      // tanks finished in the current force pass
+};
+
+// A two-float (hi + lo) compensated sum: error-free transformations keep
+// about 48 significant bits, the accuracy of an FP64 sum, on the FP32 pipe.
+struct F2 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b)
+{
+    const float s = a.hi + b.hi;                           // TwoSum(a.hi, b.hi)
+    const float bb = s - a.hi;
+    const float e = (a.hi - (s - bb)) + (b.hi - bb);
+    const float lo = e + a.lo + b.lo;
+    const float hi = s + lo;                               // FastTwoSum renormalisation
+    return F2{hi, lo - (hi - s)};
+}
+
+struct TilePartial {
+    F2 fx, fy, t;                 // fluid force / torque on the body from this tile
+    float cx, cy;                 // sum of own particle positions (sample steps only)
+    int pairs;                    // pair interactions evaluated by this tile
+    int wall;                     // 1 if any ghost pair contributed
+};
+
+// Optional per-particle outputs of an evaluation pass (indexed by particle).
+struct EvalOut {
+    float* rho;
+    float* drho;
+    float* acc;       // [N, 2]
+    int* nbr;         // [N, 3]
+    int* keys;        // [N]
+    double* body;     // [B, 6]
+};
+
+// Pointers of one simulator instance, passed by value to every kernel.
+struct SimDev {
+    const TankDev* tank;
+    BodyDev* body;
+    RunDev* run;
+    float4* pv[2];
+    int* pid[2];
+    int* count[2];
+    float2* rhoP;                 // indexed by slot of the current buffer
+    const int4* tiles;            // (tank, first cell x, first cell y, tile index within tank)
+    const int* tile_tank_first;   // per tank: first tile (size B + 1)
+    TilePartial* partials;
+    const float4* gB;             // body-frame ghost positions as two-float (x_hi, x_lo, y_hi, y_lo), sorted by ghost cell
+    const int* gstart;            // per tank (G*G + 1) ghost-cell starts (global ghost index)
+    float4* gpos;                 // per step: (hi_x, hi_y, lo_x, lo_y) world position, written by the density pass
+    float4* gvel;                 // per step: (v_x, v_y, arm_x, arm_y)
+    int B;
+    int n_tiles;
+};
+
+// ---------------------------------------------------------------------------
+// Kernel arithmetic in FP32
+// ---------------------------------------------------------------------------
+
+// Cubic spline (Eq. 22): W(r) for r < 2h.
+__device__ __forceinline__ float w_cubic(const TankDev& T, float r)
+{
+    float q = r * T.inv_h;
+    float a = 2.0f - q, b = 1.0f - q;
+    float f = a * a * a;
+    if (q < 1.0f) f -= 4.0f * b * b * b;
+    return T.cW * f;
+}
+
+// (dW/dr) / r for the cubic spline, 0 < r < 2h.
+__device__ __forceinline__ float dw_cubic_over_r(const TankDev& T, float r, float inv_r)
+{
+    float q = r * T.inv_h;
+    float a = 2.0f - q, b = 1.0f - q;
+    float fp = -3.0f * a * a;
+    if (q < 1.0f) fp += 12.0f * b * b;
+    return T.cdW * fp * inv_r;
+}
+
+// Squared distance with the exact operation sequence of the integer decisions:
+// fma(dx, dx, dy*dy) with every operation rounded to nearest.
+__device__ __forceinline__ float dist2(float dx, float dy)
+{
+    return __fmaf_rn(dx, dx, __fmul_rn(dy, dy));
+}
+
+// Grid column of x: floor(fl32(fl32(x - o) * inv)) clamped to [0, G-1]; a
+// clamped (or non-finite) position sets *out.
+__device__ __forceinline__ int cell_coord(float x, float o, float inv, int G, bool* out)
+{
+    const float f = floorf(__fmul_rn(__fsub_rn(x, o), inv));
+    if (f >= 0.0f && f <= (float)(G - 1)) return (int)f;
+    *out = true;
+    return (f > 0.0f) ? G - 1 : 0;  // NaN lands in column 0
+}
+
+}  // namespace sph

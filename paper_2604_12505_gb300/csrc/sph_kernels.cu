@@ -1,0 +1,761 @@
+// sph_kernels.cu -- the per-step kernels of the SPH sloshing simulator.
+//
+// One inner step (Algorithm 1 + symplectic Euler, Section 3.4) is two
+// launches over all tanks of a batch, chained by programmatic dependent
+// launch (each kernel lets its successor be scheduled at once and waits for
+// its predecessor only before touching data the predecessor writes):
+//   density_kernel  Eq. 21 for the ghosts each particle meets (two-float
+//                   arithmetic on the FP32 pipe), Eqs. 14 and 11 (+ the
+//                   continuity sum): one CTA per tile of TX x TY grid cells;
+//                   the tile plus a one-cell halo is staged in shared memory,
+//                   ordered by particle index inside each cell, and every own
+//                   particle sums over its 3x3 cells.
+//   force_kernel    Eqs. 10, 12 (fluid pairs), 16-19 (ghost pairs), the fluid
+//                   acceleration of Algorithm 1, kick-then-drift of the fluid,
+//                   and the re-binning of the moved particle into the other
+//                   grid buffer.  Per-tile compensated force/torque partials;
+//                   the last CTA of a tank reduces them in fixed order,
+//                   assembles them in FP64 and integrates the FP64 body
+//                   (Eq. 20), samples outputs and runs the PD law (Eq. 28).
+// No warp-wide FP64 arithmetic runs in the tile kernels: this GPU's FP64
+// pipe issues a warp instruction in about 16 cycles per SM.
+#include <cfloat>
+#include <climits>
+
+#include "sph_common.cuh"
+#include "sph_launch.h"
+
+namespace sph {
+
+template <int TX, int TY>
+struct Shape {
+    static constexpr int SX = TX + 2;
+    static constexpr int SY = TY + 2;
+    static constexpr int NC = SX * SY;       // staged cells (tile + halo)
+    static constexpr int MAXS = NC * 12;     // staged particles (1.8x the lattice mean)
+    static constexpr int THREADS = (TX * TY >= 32) ? 256 : (TX * TY >= 16 ? 128 : (TX * TY >= 8 ? 64 : 32));
+};
+
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------
+// Shared-memory staging of a tile and its halo
+// ---------------------------------------------------------------------------
+template <int TX, int TY, bool RHO>
+struct Stage {
+    using Sh = Shape<TX, TY>;
+    int start[Sh::NC + 1];
+    int own_row[TY + 1];
+    float4 pv[Sh::MAXS];
+    int pid[Sh::MAXS];
+    int pid_in[Sh::MAXS];         // particle index in global slot order (before ordering)
+    int slot[Sh::MAXS];
+    unsigned char cell[Sh::MAXS];
+    float2 rho[RHO ? Sh::MAXS : 1];
+};
+
+// Loads the counts, scans them, and gathers the particles of the (TX+2) x
+// (TY+2) staged cells, each cell ordered by particle index.  Returns false
+// (uniformly over the block) if the staged set does not fit.
+template <int TX, int TY, bool RHO>
+__device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, int cy0, Stage<TX, TY, RHO>& sm)
+{
+    using Sh = Shape<TX, TY>;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int* __restrict__ count = S.count[buf];
+    for (int c = tid; c < Sh::NC; c += blockDim.x) {
+        int ix = cx0 - 1 + c % Sh::SX, iy = cy0 - 1 + c / Sh::SX;
+        int n = 0;
+        if (ix >= 0 && ix < T.G && iy >= 0 && iy < T.G) n = min(count[T.cell_base + iy * T.G + ix], kCap);
+        sm.start[c] = n;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        int carry = 0;
+        for (int base = 0; base < Sh::NC; base += 32) {
+            int c = base + lane;
+            int v = c < Sh::NC ? sm.start[c] : 0;
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (c < Sh::NC) sm.start[c] = carry + incl - v;
+            carry += __shfl_sync(0xffffffffu, incl, 31);
+        }
+        if (lane == 0) sm.start[Sh::NC] = carry;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int r = 0; r < TY; ++r) {
+            sm.own_row[r] = acc;
+            int row = (r + 1) * Sh::SX;
+            acc += sm.start[row + TX + 1] - sm.start[row + 1];
+        }
+        sm.own_row[TY] = acc;
+    }
+    const int total = sm.start[Sh::NC];
+    if (total > Sh::MAXS) {
+        if (tid == 0) atomicOr(&S.body[S.tiles[blockIdx.x].x].flags, SPH_FLAG_STAGE_FULL);
+        __syncthreads();
+        return false;
+    }
+    // pass 1: every staged slot at once -- its cell (binary search) and particle index
+    for (int e = tid; e < total; e += blockDim.x) {
+        int lo = 0, hi = Sh::NC;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (sm.start[mid] <= e) lo = mid; else hi = mid;
+        }
+        const int ix = cx0 - 1 + lo % Sh::SX, iy = cy0 - 1 + lo / Sh::SX;
+        sm.cell[e] = (unsigned char)lo;
+        sm.pid_in[e] = S.pid[buf][(T.cell_base + iy * T.G + ix) * kCap + (e - sm.start[lo])];
+    }
+    __syncthreads();
+    // pass 2: rank by particle index inside the cell and gather into that
+    // order (reads only cell[], pid_in[] and start[], which pass 2 never writes)
+#pragma unroll 2
+    for (int e = tid; e < total; e += blockDim.x) {
+        const int c = sm.cell[e];
+        const int a = sm.start[c];
+        const int id = sm.pid_in[e];
+        int rank = 0;
+        for (int j = a; j < sm.start[c + 1]; ++j) rank += (sm.pid_in[j] < id);
+        const int d = a + rank;
+        const int ix = cx0 - 1 + c % Sh::SX, iy = cy0 - 1 + c / Sh::SX;
+        const int gs = (T.cell_base + iy * T.G + ix) * kCap + (e - a);
+        sm.pv[d] = S.pv[buf][gs];
+        if (RHO) sm.rho[d] = S.rhoP[gs];
+        sm.pid[d] = id;
+        sm.slot[d] = gs;
+    }
+    __syncthreads();
+    return true;
+}
+
+// Smem index of the t-th own particle (own cells are TY contiguous row runs).
+template <int TX, int TY, bool RHO>
+__device__ __forceinline__ int own_index(int t, const Stage<TX, TY, RHO>& sm)
+{
+    using Sh = Shape<TX, TY>;
+    int r = 0;
+#pragma unroll
+    for (int q = 1; q < TY; ++q) r += (t >= sm.own_row[q]);
+    return sm.start[(r + 1) * Sh::SX + 1] + (t - sm.own_row[r]);
+}
+
+// Visits the ghosts of the 3x3 body-frame ghost cells around a fluid
+// particle; the body-frame position only selects cells, so FP32 suffices.
+template <class F>
+__device__ __forceinline__ void for_ghosts(const SimDev& S, const TankDev& T, float xi, float yi, float bc, float bs,
+                                           float brx, float bry, F&& f)
+{
+    float px = xi - brx, py = yi - bry;
+    float ex = bc * px + bs * py, ey = bc * py - bs * px;
+    if (ex * ex + ey * ey < T.ghost_rin2) return;
+    const float fx = floorf((ex - T.g_orig) * T.g_inv_cell), fy = floorf((ey - T.g_orig) * T.g_inv_cell);
+    if (!(fx >= -1.0f && fx <= (float)T.G && fy >= -1.0f && fy <= (float)T.G)) return;  // off the grid or NaN
+    const int gx = (int)fx, gy = (int)fy;
+    int x0 = max(gx - 1, 0), x1 = min(gx + 1, T.G - 1);
+    if (x0 > x1) return;
+    for (int yy = max(gy - 1, 0); yy <= min(gy + 1, T.G - 1); ++yy) {
+        int row = T.gcell_base + yy * T.G;
+        int a = __ldg(S.gstart + row + x0), b = __ldg(S.gstart + row + x1 + 1);
+        for (int j = a; j < b; ++j) f(j);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Density pass: Eqs. 14, 11 (+ continuity sum)
+// ---------------------------------------------------------------------------
+template <int TX, int TY>
+__global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev S, EvalOut E, int eval)
+{
+    using Sh = Shape<TX, TY>;
+    __shared__ Stage<TX, TY, false> sm;
+    pdl_trigger();
+    const int4 td = S.tiles[blockIdx.x];
+    const TankDev& T = S.tank[td.x];
+    const int cx0 = td.y, cy0 = td.z;
+    pdl_wait();
+    const int buf = (int)(S.run->step & 1), nbuf = buf ^ 1;
+
+    // clear the other buffer's counts of the own cells (it is re-filled by the force pass)
+    for (int c = threadIdx.x; c < TX * TY; c += blockDim.x) {
+        int ix = cx0 + c % TX, iy = cy0 + c / TX;
+        if (ix < T.G && iy < T.G) S.count[nbuf][T.cell_base + iy * T.G + ix] = 0;
+    }
+    if (!stage_tile<TX, TY, false>(S, T, buf, cx0, cy0, sm)) return;
+    const int n_own = sm.own_row[TY];
+    if (n_own == 0) return;
+
+    const BodyDev& b = S.body[td.x];
+    const float bc = b.fc, bs = b.fs, brx = b.frx, bry = b.fry;
+    const float2 dc = b.dc, ds = b.ds, drx = b.drx, dry = b.dry;
+    const float fvx = b.fvx, fvy = b.fvy, fw = b.fw;
+    const bool want_drho = eval && E.drho;
+
+    for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
+        const int e = own_index(t, sm);
+        const float4 pi = sm.pv[e];
+        const int c = sm.cell[e];
+        float Sf = 0.f, Df = 0.f;
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+            const int a = sm.start[c + dy * Sh::SX - 1], z = sm.start[c + dy * Sh::SX + 2];
+            for (int j = a; j < z; ++j) {
+                const float4 pj = sm.pv[j];
+                const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);
+                const float r2 = dist2(ddx, ddy);
+                if (r2 < T.R2) {
+                    const float inv_r = rsqrtf(r2);
+                    const float r = r2 * inv_r;
+                    Sf += (r2 > 0.f) ? w_cubic(T, r) : T.cW * 4.0f;
+                    if (want_drho && j != e && r2 > 0.f)
+                        Df += ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * dw_cubic_over_r(T, r, inv_r);
+                }
+            }
+        }
+        float Sg = 0.f, Dg = 0.f;
+        int ng2 = 0;
+        for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
+            // Eq. 21 in two-float arithmetic: arm = R(theta) r_g^B, r_g = r + arm,
+            // v_g = rdot + thetadot z x arm; stored for the force pass
+            const float4 gb = __ldg(S.gB + g);
+            const float2 bx = make_float2(gb.x, gb.y), by = make_float2(gb.z, gb.w);
+            const float2 sby = df_mul(ds, by);
+            const float2 ax = df_add(df_mul(dc, bx), make_float2(-sby.x, -sby.y));
+            const float2 ay = df_add(df_mul(ds, bx), df_mul(dc, by));
+            const float2 gx = df_add(drx, ax), gy = df_add(dry, ay);
+            const float armx = ax.x + ax.y, army = ay.x + ay.y;
+            const float vgx = fvx - fw * army, vgy = fvy + fw * armx;
+            S.gpos[g] = make_float4(gx.x, gy.x, gx.y, gy.y);
+            S.gvel[g] = make_float4(vgx, vgy, armx, army);
+            const float ddx = __fsub_rn(__fsub_rn(pi.x, gx.x), gx.y);
+            const float ddy = __fsub_rn(__fsub_rn(pi.y, gy.x), gy.y);
+            const float r2 = dist2(ddx, ddy);
+            if (r2 < T.R2) {
+                ++ng2;
+                const float inv_r = rsqrtf(r2);
+                const float r = r2 * inv_r;
+                Sg += (r2 > 0.f) ? w_cubic(T, r) : T.cW * 4.0f;
+                if (want_drho && r2 > 0.f)
+                    Dg += ((pi.z - vgx) * ddx + (pi.w - vgy) * ddy) * dw_cubic_over_r(T, r, inv_r);
+            }
+        });
+        const float rho = T.m * (Sf + T.gamma1 * Sg);          // Eq. 14
+        const float P = T.k * (rho - T.rho0);                  // Eq. 11
+        S.rhoP[sm.slot[e]] = make_float2(rho, P / (rho * rho));
+        if (eval) {
+            const int id = sm.pid[e];
+            if (E.rho) E.rho[id] = rho;
+            if (E.drho) E.drho[id] = T.m * (Df + T.gamma1 * Dg);
+            if (E.nbr) E.nbr[3 * id + 1] = ng2;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Block reductions (fixed order: deterministic)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ F2 shfl_down_f2(F2 v, int o)
+{
+    return F2{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+
+struct Red {
+    F2 fx, fy, t, cx, cy;
+    unsigned long long pairs;
+};
+
+// Sums over the block (result valid in thread 0).  Only the parts flagged
+// by the uniform switches are reduced.
+__device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* >= 32 */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (forces) {
+            r.fx = f2_add(r.fx, shfl_down_f2(r.fx, o));
+            r.fy = f2_add(r.fy, shfl_down_f2(r.fy, o));
+            r.t = f2_add(r.t, shfl_down_f2(r.t, o));
+        }
+        if (com) {
+            r.cx = f2_add(r.cx, shfl_down_f2(r.cx, o));
+            r.cy = f2_add(r.cy, shfl_down_f2(r.cy, o));
+        }
+        r.pairs += __shfl_down_sync(0xffffffffu, r.pairs, o);
+    }
+    __syncthreads();
+    if (lane == 0) scratch[warp] = r;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < nw; ++w) {
+            if (forces) {
+                r.fx = f2_add(r.fx, scratch[w].fx);
+                r.fy = f2_add(r.fy, scratch[w].fy);
+                r.t = f2_add(r.t, scratch[w].t);
+            }
+            if (com) {
+                r.cx = f2_add(r.cx, scratch[w].cx);
+                r.cy = f2_add(r.cy, scratch[w].cy);
+            }
+            r.pairs += scratch[w].pairs;
+        }
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Body update by the last CTA of a tank (Eq. 20, Eq. 28, outputs)
+// ---------------------------------------------------------------------------
+__device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
+                              Red* scratch)
+{
+    __threadfence();
+    RunDev* run = S.run;
+    const long long step = run->step;
+    const bool sample = !eval && (step % T.outer_every) == 0;
+    const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
+    const F2 z{0.f, 0.f};
+    Red r{z, z, z, z, z, 0ull};
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
+        const TilePartial* P = S.partials + t;
+        if (__ldcg(&P->wall)) {
+            r.fx = f2_add(r.fx, F2{__ldcg(&P->fx.hi), __ldcg(&P->fx.lo)});
+            r.fy = f2_add(r.fy, F2{__ldcg(&P->fy.hi), __ldcg(&P->fy.lo)});
+            r.t = f2_add(r.t, F2{__ldcg(&P->t.hi), __ldcg(&P->t.lo)});
+        }
+        if (sample) {
+            r.cx = f2_add(r.cx, F2{__ldcg(&P->cx), 0.f});
+            r.cy = f2_add(r.cy, F2{__ldcg(&P->cy), 0.f});
+        }
+        r.pairs += (unsigned long long)__ldcg(&P->pairs);
+    }
+    r = block_reduce(r, true, sample, scratch);
+    if (threadIdx.x != 0) return;
+
+    // FP64 from here on: assembly of the reduced force/torque and the body
+    const double Fx = (double)r.fx.hi + (double)r.fx.lo;
+    const double Fy = (double)r.fy.hi + (double)r.fy.lo;
+    const double Tq = (double)r.t.hi + (double)r.t.lo;
+    BodyDev& b = S.body[tank];
+    const long long k = step - run->step0;
+    double ux = 0.0, uy = 0.0, ut = 0.0;
+    if (run->u) {
+        const double* u = run->u + tank * run->u_tank_stride + 3 * k;
+        ux = u[0];
+        uy = u[1];
+        ut = u[2];
+    }
+    if (sample) {
+        const long long oe = T.outer_every;
+        const long long row = step / oe - (run->step0 + oe - 1) / oe;
+        if (run->ctrl_on) {  // Eq. 28 under zero-order hold
+            const double ref = run->theta_ref ? run->theta_ref[tank * run->ref_stride + row] : 0.0;
+            const double Jc = run->ctrl_J > 0.0 ? run->ctrl_J : T.J_body;
+            b.tau_c = Jc * run->ctrl_w * run->ctrl_w * (ref - b.th) - 2.0 * run->ctrl_xi * Jc * run->ctrl_w * b.w;
+        }
+        if (run->y) {
+            double* y = run->y + tank * run->y_tank_stride + row * SPH_NY;
+            y[0] = b.r[0];
+            y[1] = b.r[1];
+            y[2] = b.th;
+            y[3] = b.v[0];
+            y[4] = b.v[1];
+            y[5] = b.w;
+            y[6] = Fx;
+            y[7] = Fy;
+            y[8] = Tq;
+            y[9] = T.n_f ? ((double)r.cx.hi + (double)r.cx.lo) / T.n_f : 0.0;
+            y[10] = T.n_f ? ((double)r.cy.hi + (double)r.cy.lo) / T.n_f : 0.0;
+        }
+    }
+    const double tau = ut + (run->ctrl_on ? b.tau_c : 0.0);
+    const double ax = (Fx + ux) / T.m_body, ay = (Fy + uy) / T.m_body, aw = (Tq + tau) / T.J_body;
+    if (eval) {
+        if (E.body) {
+            double* o = E.body + 6 * tank;
+            o[0] = Fx;
+            o[1] = Fy;
+            o[2] = Tq;
+            o[3] = ax;
+            o[4] = ay;
+            o[5] = aw;
+        }
+    } else {
+        b.anchor[nbuf][0] = b.r[0];
+        b.anchor[nbuf][1] = b.r[1];
+        if (!run->body_fixed) {
+            b.v[0] += T.dt_d * ax;  // kick then drift (Section 3.4)
+            b.v[1] += T.dt_d * ay;
+            b.w += T.dt_d * aw;
+            b.r[0] += T.dt_d * b.v[0];
+            b.r[1] += T.dt_d * b.v[1];
+            b.th += T.dt_d * b.w;
+            sincos(b.th, &b.s, &b.c);
+        }
+        b.dc = df_split(b.c);
+        b.ds = df_split(b.s);
+        b.drx = df_split(b.r[0]);
+        b.dry = df_split(b.r[1]);
+        b.fvx = (float)b.v[0];
+        b.fvy = (float)b.v[1];
+        b.fw = (float)b.w;
+        b.fc = (float)b.c;
+        b.fs = (float)b.s;
+        b.frx = (float)b.r[0];
+        b.fry = (float)b.r[1];
+        b.fo_next[0] = (float)(b.r[0] - T.W);
+        b.fo_next[1] = (float)(b.r[1] - T.W);
+        b.pairs += r.pairs;
+    }
+    b.done = 0;
+    __threadfence();
+    const unsigned prev = atomicAdd(&run->tanks_done, 1u);
+    if (prev == (unsigned)S.B - 1) {
+        if (!eval) run->step = step + 1;
+        run->tanks_done = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Force pass: Eqs. 10, 12, 16-19, Algorithm 1, symplectic Euler, re-binning
+// ---------------------------------------------------------------------------
+template <int TX, int TY>
+__global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S, EvalOut E, int eval)
+{
+    using Sh = Shape<TX, TY>;
+    __shared__ Stage<TX, TY, true> sm;
+    __shared__ Red scratch[32];
+    __shared__ int is_last;
+    pdl_trigger();
+    const int4 td = S.tiles[blockIdx.x];
+    const int tank = td.x;
+    const TankDev& T = S.tank[tank];
+    const int cx0 = td.y, cy0 = td.z;
+    pdl_wait();
+    const long long step = S.run->step;
+    const int buf = (int)(step & 1), nbuf = buf ^ 1;
+    const bool sample = !eval && (step % T.outer_every) == 0;
+    const float damp = 1.0f - S.run->damping;
+
+    const F2 z{0.f, 0.f};
+    Red acc{z, z, z, z, z, 0ull};
+    int flags = 0, wall = 0;
+    if (stage_tile<TX, TY, true>(S, T, buf, cx0, cy0, sm)) {
+        const BodyDev& b = S.body[tank];
+        const float bc = b.fc, bs = b.fs, brx = b.frx, bry = b.fry;
+        const float ox = b.fo_next[0], oy = b.fo_next[1];  // origin of the next grid
+        const int n_own = sm.own_row[TY];
+        const float mm = T.m * T.m;
+        float wfx = 0.f, wfy = 0.f, wt = 0.f, cxs = 0.f, cys = 0.f;
+        for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
+            const int e = own_index(t, sm);
+            const float4 pi = sm.pv[e];
+            const float2 ri = sm.rho[e];
+            const int c = sm.cell[e];
+            float ax = 0.f, ay = 0.f;
+            int nff = 0;
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int a = sm.start[c + dy * Sh::SX - 1], zz = sm.start[c + dy * Sh::SX + 2];
+                for (int j = a; j < zz; ++j) {
+                    const float4 pj = sm.pv[j];
+                    const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);
+                    const float r2 = dist2(ddx, ddy);
+                    if (r2 < T.R2 && j != e) {
+                        ++nff;
+                        if (r2 > 0.f) {
+                            const float2 rj = sm.rho[j];
+                            const float inv_r = rsqrtf(r2);
+                            const float r = r2 * inv_r;
+                            const float gW = dw_cubic_over_r(T, r, inv_r);
+                            const float press = -(ri.y + rj.y);                          // Eq. 10
+                            const float vr = (pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy;
+                            const float visc = __fdividef(T.visc_a * vr, (ri.x + rj.x) * (r2 + T.epsh2));  // Eq. 12
+                            const float s = T.m * (press + visc) * gW;
+                            ax = fmaf(s, ddx, ax);
+                            ay = fmaf(s, ddy, ay);
+                        }
+                    }
+                }
+            }
+            int nfg = 0;
+            for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
+                const float4 gp = __ldg(S.gpos + g);
+                const float ddx = __fsub_rn(__fsub_rn(pi.x, gp.x), gp.z);
+                const float ddy = __fsub_rn(__fsub_rn(pi.y, gp.y), gp.w);
+                const float r2 = dist2(ddx, ddy);
+                if (r2 < T.h2) {
+                    ++nfg;
+                    if (r2 > 0.f) {
+                        const float4 gv = __ldg(S.gvel + g);
+                        const float inv_r = rsqrtf(r2);
+                        const float r = r2 * inv_r;
+                        const float d = T.h - r;
+                        const float gWs = T.cdS * d * d * inv_r;                         // (dW_s3/dr)/r
+                        const float fp = T.gp_sign * 2.0f * mm * ri.y * gWs;            // Eq. 16
+                        const float vr = (pi.z - gv.x) * ddx + (pi.w - gv.y) * ddy;
+                        const float fv = __fdividef(mm * T.beta2 * fminf(vr, 0.f), (ri.x + ri.x) * (r2 + T.epsh2)) * gWs;  // Eq. 18
+                        const float f = fp + fv;
+                        const float fx = f * ddx, fy = f * ddy;
+                        ax = fmaf(fx, T.inv_m, ax);
+                        ay = fmaf(fy, T.inv_m, ay);
+                        wfx -= fx;                                                       // Eqs. 17, 19
+                        wfy -= fy;
+                        wt -= gv.z * fy - gv.w * fx;                                     // Eq. 20 torque
+                    }
+                }
+            });
+            wall |= (nfg > 0);
+            acc.pairs += (unsigned long long)(nff + nfg);
+            cxs += pi.x;
+            cys += pi.y;
+            ax += T.grav_x;
+            ay += T.grav_y;
+            const int id = sm.pid[e];
+            if (eval) {
+                if (E.acc) {
+                    E.acc[2 * id] = ax;
+                    E.acc[2 * id + 1] = ay;
+                }
+                if (E.nbr) {
+                    E.nbr[3 * id] = nff;
+                    E.nbr[3 * id + 2] = nfg;
+                }
+                if (E.keys) E.keys[id] = (cy0 - 1 + c / Sh::SX) * T.G + (cx0 - 1 + c % Sh::SX);
+            } else {
+                // kick then drift (Section 3.4), then bin into the next grid
+                const float vx = fmaf(T.dt, ax, pi.z) * damp, vy = fmaf(T.dt, ay, pi.w) * damp;
+                const float x = fmaf(T.dt, vx, pi.x), y = fmaf(T.dt, vy, pi.y);
+                if (!(isfinite(x) && isfinite(y) && isfinite(vx) && isfinite(vy))) flags |= SPH_FLAG_NAN;
+                bool out = false;
+                const int ccx = cell_coord(x, ox, T.inv_cell, T.G, &out);
+                const int ccy = cell_coord(y, oy, T.inv_cell, T.G, &out);
+                if (out) flags |= SPH_FLAG_ESCAPED;
+                const int cell = T.cell_base + ccy * T.G + ccx;
+                const int slot = atomicAdd(&S.count[nbuf][cell], 1);
+                if (slot < kCap) {
+                    S.pv[nbuf][cell * kCap + slot] = make_float4(x, y, vx, vy);
+                    S.pid[nbuf][cell * kCap + slot] = id;
+                } else {
+                    flags |= SPH_FLAG_CELL_FULL;
+                }
+            }
+        }
+        acc.fx = F2{wfx, 0.f};
+        acc.fy = F2{wfy, 0.f};
+        acc.t = F2{wt, 0.f};
+        acc.cx = F2{cxs, 0.f};
+        acc.cy = F2{cys, 0.f};
+    }
+    if (flags) atomicOr(&S.body[tank].flags, flags);
+    const bool any_wall = __syncthreads_or(wall) != 0;
+    Red r = block_reduce(acc, any_wall, sample, scratch);
+    if (threadIdx.x == 0) {
+        TilePartial P;
+        P.fx = r.fx;
+        P.fy = r.fy;
+        P.t = r.t;
+        P.cx = r.cx.hi + r.cx.lo;
+        P.cy = r.cy.hi + r.cy.lo;
+        P.pairs = (int)r.pairs;
+        P.wall = any_wall ? 1 : 0;
+        S.partials[blockIdx.x] = P;
+        __threadfence();
+        const unsigned n_tiles = (unsigned)(S.tile_tank_first[tank + 1] - S.tile_tank_first[tank]);
+        is_last = (atomicAdd(&S.body[tank].done, 1u) == n_tiles - 1);
+    }
+    __syncthreads();
+    if (is_last) tank_finalize(S, T, tank, eval, E, nbuf, scratch);
+}
+
+// ---------------------------------------------------------------------------
+// State transfer and bookkeeping kernels
+// ---------------------------------------------------------------------------
+
+// Bins flat particles [N, 4] (tanks concatenated) into grid buffer `buf`,
+// anchored at each tank's stored anchor for that buffer.
+__global__ void bin_flat_kernel(SimDev S, const float4* __restrict__ xv, const int* __restrict__ part_tank, int n,
+                                int buf)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int t = part_tank[i];
+    const TankDev& T = S.tank[t];
+    const BodyDev& b = S.body[t];
+    const float4 p = xv[i];
+    const float ox = (float)(b.anchor[buf][0] - T.W), oy = (float)(b.anchor[buf][1] - T.W);
+    bool out = false;
+    const int cx = cell_coord(p.x, ox, T.inv_cell, T.G, &out), cy = cell_coord(p.y, oy, T.inv_cell, T.G, &out);
+    int flags = out ? SPH_FLAG_ESCAPED : 0;
+    if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w))) flags |= SPH_FLAG_NAN;
+    const int cell = T.cell_base + cy * T.G + cx;
+    const int slot = atomicAdd(&S.count[buf][cell], 1);
+    if (slot < kCap) {
+        S.pv[buf][cell * kCap + slot] = p;
+        S.pid[buf][cell * kCap + slot] = i;
+    } else {
+        flags |= SPH_FLAG_CELL_FULL;
+    }
+    if (flags) atomicOr(&S.body[t].flags, flags);
+}
+
+// Writes the body state [B, 6] and derived quantities; anchors buffer `buf`.
+__global__ void set_body_kernel(SimDev S, const double* __restrict__ body, int buf)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.B) return;
+    BodyDev& b = S.body[t];
+    const TankDev& T = S.tank[t];
+    const double* s = body + 6 * t;
+    b.r[0] = s[0];
+    b.r[1] = s[1];
+    b.th = s[2];
+    b.v[0] = s[3];
+    b.v[1] = s[4];
+    b.w = s[5];
+    sincos(b.th, &b.s, &b.c);
+    b.anchor[buf][0] = s[0];
+    b.anchor[buf][1] = s[1];
+    b.tau_c = 0.0;
+    b.done = 0;
+    b.dc = df_split(b.c);
+    b.ds = df_split(b.s);
+    b.drx = df_split(b.r[0]);
+    b.dry = df_split(b.r[1]);
+    b.fvx = (float)b.v[0];
+    b.fvy = (float)b.v[1];
+    b.fw = (float)b.w;
+    b.fc = (float)b.c;
+    b.fs = (float)b.s;
+    b.frx = (float)b.r[0];
+    b.fry = (float)b.r[1];
+    b.fo_next[0] = (float)(b.r[0] - T.W);
+    b.fo_next[1] = (float)(b.r[1] - T.W);
+}
+
+__global__ void get_body_kernel(SimDev S, double* __restrict__ body)
+{
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.B) return;
+    const BodyDev& b = S.body[t];
+    double* o = body + 6 * t;
+    o[0] = b.r[0];
+    o[1] = b.r[1];
+    o[2] = b.th;
+    o[3] = b.v[0];
+    o[4] = b.v[1];
+    o[5] = b.w;
+}
+
+// One warp per cell: scatter the occupied slots of buffer `buf` to [N, 4].
+__global__ void gather_state_kernel(SimDev S, float4* __restrict__ xv, int n_cells_total, int buf)
+{
+    const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (cell >= n_cells_total) return;
+    const int n = min(S.count[buf][cell], kCap);
+    if (lane < n) {
+        const int gs = cell * kCap + lane;
+        xv[S.pid[buf][gs]] = S.pv[buf][gs];
+    }
+}
+
+__global__ void set_run_kernel(RunDev* run, RunDev desc)
+{
+    desc.step = run->step;
+    desc.step0 = run->step;
+    desc.tanks_done = 0;
+    *run = desc;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers
+// ---------------------------------------------------------------------------
+template <typename... KArgs, typename... Args>
+static cudaError_t launch(void (*k)(KArgs...), int grid, int block, cudaStream_t st, bool pdl, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = pdl ? at : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
+template <int TX, int TY>
+static cudaError_t launch_tile_phase(const SimDev& S, const EvalOut& E, int eval, int n_tiles, int phase,
+                                     cudaStream_t st, bool pdl)
+{
+    using Sh = Shape<TX, TY>;
+    if (phase == 0) return launch(density_kernel<TX, TY>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+    return launch(force_kernel<TX, TY>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+}
+
+void tile_dims(int code, int* tx, int* ty)
+{
+    static const int T[SPH_TILE_COUNT][2] = {{2, 2}, {4, 2}, {4, 4}, {8, 4}, {8, 8}};
+    *tx = T[code - 1][0];
+    *ty = T[code - 1][1];
+}
+
+// phase 0: density pass, phase 1: force pass
+cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, int phase,
+                         cudaStream_t st, bool pdl)
+{
+    switch (tile_code) {
+    case 1: return launch_tile_phase<2, 2>(S, E, eval, n_tiles, phase, st, pdl);
+    case 2: return launch_tile_phase<4, 2>(S, E, eval, n_tiles, phase, st, pdl);
+    case 3: return launch_tile_phase<4, 4>(S, E, eval, n_tiles, phase, st, pdl);
+    case 4: return launch_tile_phase<8, 4>(S, E, eval, n_tiles, phase, st, pdl);
+    case 5: return launch_tile_phase<8, 8>(S, E, eval, n_tiles, phase, st, pdl);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, cudaStream_t st,
+                        bool pdl)
+{
+    for (int ph = 0; ph < 2; ++ph) {
+        cudaError_t e = launch_phase(S, E, eval, tile_code, n_tiles, ph, st, pdl);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_bin_flat(const SimDev& S, const float* xv, const int* part_tank, int n, int buf, cudaStream_t st)
+{
+    if (n > 0) bin_flat_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, (const float4*)xv, part_tank, n, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_body(const SimDev& S, const double* body, int buf, cudaStream_t st)
+{
+    set_body_kernel<<<(S.B + 127) / 128, 128, 0, st>>>(S, body, buf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_get_state(const SimDev& S, float* xv, double* body, int n_cells_total, int buf, cudaStream_t st)
+{
+    if (xv && n_cells_total > 0) gather_state_kernel<<<(n_cells_total + 7) / 8, 256, 0, st>>>(S, (float4*)xv, n_cells_total, buf);
+    if (body) get_body_kernel<<<(S.B + 127) / 128, 128, 0, st>>>(S, body);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_set_run(RunDev* run, const RunDev& desc, cudaStream_t st)
+{
+    set_run_kernel<<<1, 1, 0, st>>>(run, desc);
+    return cudaGetLastError();
+}
+
+}  // namespace sph

@@ -48,3 +48,13 @@ def test_fp32_neighbour_counts_agree_with_exact_distances(orc):
     assert np.all(np.abs(nfg2 - (dg < (2 * h) ** 2).sum(1)) <= (np.abs(dg - 4 * h * h) < 4e-5 * h * h).sum(1))
     assert np.all(np.abs(nfg1 - (dg < h * h).sum(1)) <= (np.abs(dg - h * h) < 1e-5 * h * h).sum(1))
     assert nff.sum() > 10 * len(x) and nfg1.sum() > 0
+
+
+def test_pair_count_equals_fp32_counts_away_from_the_support(orc):
+    p = orc.params(**W.TINY)
+    x, gB = orc.tank(p)
+    body = np.array([0.0, 0.0, 0.2, 0.0, 0.0, 0.0])
+    x = x + W.perturbation(x.shape, 0.2 * p.dx, seed=13)
+    nff, _, nfg1 = orc.neighbor_counts_f32(p, x.astype(np.float32), gB, body)
+    x32 = x.astype(np.float32).astype(np.float64)
+    assert orc.pair_count(p, x32, gB, body) == int(nff.sum() + nfg1.sum())

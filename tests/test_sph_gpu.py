@@ -1,0 +1,275 @@
+"""GPU parity of the SPH step against the FP64 oracle (through the C ABI).
+
+Tolerances (per-step, one evaluation from the identical FP32 state):
+  density         max_i |rho_gpu - rho_ref| / rho_ref          <= 1e-5
+  acceleration    max_i |a_gpu - a_ref| / max_i |a_ref|         <= 1e-5
+  continuity sum  same norm-wise measure                        <= 1e-4
+  body force      |F_gpu - F_ref| <= 1e-5 * m * sum_i |a_ref_i|   (sum of FP32 pair
+                  forces reduced in FP64: error scales with the summed magnitude)
+  integer keys and neighbour counts: bit-exact.
+Trajectories over the first 200 steps: for each group of the output record
+(body position r, angle, body velocity, angular rate, fluid centre of mass)
+max_t ||q_gpu - q_ref|| / max_t ||q_ref|| <= 1e-3 (vector norms: a component
+that vanishes by the tank's mirror symmetry is not divided by its own noise),
+and every particle's position within 1e-3 of the largest displacement.
+"""
+import numpy as np
+import pytest
+
+from paper_2604_12505_gb300 import workloads as W
+from tests.gpu_util import need_gpu, normwise, oracle_state, traj_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    return need_gpu()
+
+
+def _sim(cfg):
+    from paper_2604_12505_gb300.sph import Sim
+    return Sim(cfg)
+
+
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("cfg", [W.TINY, W.SMALL, W.JVP])
+def test_tank_builder_matches_oracle(torch_mod, orc, cfg):
+    p = orc.params(**cfg)
+    x, gB = orc.tank(p)
+    with _sim(cfg) as s:
+        assert s.n_fluid == [x.shape[0]] and s.n_ghost == [gB.shape[0]]
+        np.testing.assert_array_equal(s.ghosts_body(0), gB)
+        xv, body = s.state()
+        np.testing.assert_array_equal(xv.cpu().numpy()[:, :2], x.astype(np.float32))
+        assert np.all(xv.cpu().numpy()[:, 2:] == 0) and np.all(body.cpu().numpy() == 0)
+
+
+@pytest.mark.parametrize("cfg,pos,vel,body", [
+    (W.TINY, 0.2, 0.3, [0.004, -0.003, 0.4, 0.1, -0.05, 0.7]),
+    (W.SMALL, 0.0, 0.0, [0.0] * 6),
+    (W.SMALL, 0.25, 0.5, [0.013, 0.021, -1.3, 0.2, 0.1, -0.9]),
+    (dict(W.SMALL, ghost_pressure_sign=1.0, gamma1=1.0), 0.2, 0.4, [0.0, 0.0, 0.3, 0.0, 0.0, 0.2]),
+])
+def test_one_step_eval_parity(torch_mod, orc, cfg, pos, vel, body):
+    torch = torch_mod
+    xv, x, v, gB, p = oracle_state(orc, cfg, pos, vel, seed=21)
+    body = np.array(body, dtype=np.float64)
+    u = np.array([3.0, -2.0, 1.5])
+    ref = orc.evaluate(p, x, v, gB, body, u=u)
+    with _sim(cfg) as s:
+        s.set_state(xv, body)
+        out = s.eval(u=u[None])
+        torch.cuda.synchronize()
+        s.check()
+        rho = out["rho"].cpu().numpy()
+        acc = out["acc"].cpu().numpy()
+        drho = out["drho"].cpu().numpy()
+        nbr = out["nbr"].cpu().numpy()
+        keys = out["keys"].cpu().numpy()
+        bo = out["body"].cpu().numpy()[0]
+        cell, Wd, G, anchor = s.grid_info(0)
+    assert np.abs(rho - ref["rho"]).max() / ref["rho"].min() <= 1e-5
+    assert normwise(acc, ref["acc"]) <= 1e-5
+    assert normwise(drho, ref["drho"]) <= 1e-4
+    m = orc.mass_of(p)
+    scale = m * np.linalg.norm(ref["acc"], axis=1).sum()
+    assert np.abs(bo[:3] - ref["fb"]).max() <= 1e-5 * scale
+    ba_scale = np.array([scale / p.m_body, scale / p.m_body, scale * p.R / p.J_body])
+    assert np.all(np.abs(bo[3:] - ref["body_acc"]) <= 1e-5 * ba_scale + 1e-12)
+    # integer decisions: bit-exact
+    np.testing.assert_array_equal(keys, orc.cell_keys_f32(p, xv[:, :2], anchor))
+    nff, nfg2, nfg1 = orc.neighbor_counts_f32(p, xv[:, :2], gB, body)
+    np.testing.assert_array_equal(nbr[:, 0], nff)
+    np.testing.assert_array_equal(nbr[:, 1], nfg2)
+    np.testing.assert_array_equal(nbr[:, 2], nfg1)
+
+
+@pytest.mark.parametrize("ctrl", [False, True])
+def test_trajectory_parity_200_steps(torch_mod, orc, ctrl):
+    cfg = dict(W.SMALL, outer_every=5)
+    n = 200
+    u = W.small_torque_pulse(n, cfg["dt"], tau=2000.0, t_on=0.005)
+    u[:, 0] = 300.0
+    xv, x, v, gB, p = oracle_state(orc, cfg)
+    ref_theta = np.full(n // 5, 0.05)
+    kw = dict(theta_ref=ref_theta, use_ctrl=True) if ctrl else {}
+    xr, vr, _, yr, _ = orc.run(p, x, v, gB, np.zeros(6), n, u=u, **kw)
+    with _sim(cfg) as s:
+        y = s.step(n, u=u[None], ctrl=dict(omega=cfg["ctrl_omega"], xi=cfg["ctrl_xi"]) if ctrl else None,
+                   theta_ref=ref_theta[None] if ctrl else None)
+        s.check()
+        yg = y.cpu().numpy()[0]
+        xg = s.state()[0].cpu().numpy().astype(np.float64)
+    assert yg.shape == yr.shape
+    err = traj_err(yg, yr)
+    assert max(err.values()) <= 1e-3, err
+    # every particle: position error relative to the largest displacement, velocity norm-wise
+    disp = np.linalg.norm(xr - x, axis=1).max()
+    assert np.linalg.norm(xg[:, :2] - xr, axis=1).max() <= 1e-3 * disp
+    assert normwise(xg[:, 2:], vr) <= 1e-3
+
+
+def test_force_torque_rms_long_run(torch_mod, orc):
+    # 2000 steps of the small tank after a 1 N m torque for 0.05 s.
+    cfg = W.SMALL
+    n = 2000
+    u = W.small_torque_pulse(n, cfg["dt"], tau=1.0, t_on=0.05)
+    xv, x, v, gB, p = oracle_state(orc, cfg)
+    _, _, _, yr, _ = orc.run(p, x, v, gB, np.zeros(6), n, u=u)
+    with _sim(cfg) as s:
+        y = s.step(n, u=u[None])
+        s.check()
+        yg = y.cpu().numpy()[0]
+    for c in (6, 7, 8):
+        rms_g = np.sqrt(np.mean(yg[:, c] ** 2))
+        rms_r = np.sqrt(np.mean(yr[:, c] ** 2))
+        assert abs(rms_g - rms_r) <= 0.02 * rms_r, (c, rms_g, rms_r)
+
+
+def test_large_tank_full_size_parity(torch_mod, orc):
+    # The 97,748-particle tank in the graph-captured launch configuration of
+    # the benchmark: one evaluation plus 20 steps against the oracle.
+    cfg = W.LARGE
+    xv, x, v, gB, p = oracle_state(orc, cfg)
+    ref = orc.evaluate(p, x, v, gB, np.zeros(6))
+    n = 20
+    u = W.bang_bang_slew(n, cfg["dt"], tau=200.0)
+    u[:, 0], u[:, 1] = 400.0, -250.0
+    _, _, _, yr, _ = orc.run(p, x, v, gB, np.zeros(6), n, u=u)
+    with _sim(cfg) as s:
+        out = s.eval()
+        rho = out["rho"].cpu().numpy()
+        acc = out["acc"].cpu().numpy()
+        nbr = out["nbr"].cpu().numpy()
+        y = s.step(n, u=u[None])
+        s.check()
+        yg = y.cpu().numpy()[0]
+    assert np.abs(rho - ref["rho"]).max() / ref["rho"].min() <= 1e-5
+    assert normwise(acc, ref["acc"]) <= 1e-5
+    rng = np.random.default_rng(5)
+    q = rng.choice(x.shape[0], 400, replace=False)
+    nff, nfg2, nfg1 = orc.neighbor_counts_f32(p, xv[:, :2], gB, np.zeros(6), query=q)
+    np.testing.assert_array_equal(nbr[q, 0], nff)
+    np.testing.assert_array_equal(nbr[q, 1], nfg2)
+    np.testing.assert_array_equal(nbr[q, 2], nfg1)
+    err = traj_err(yg, yr)
+    assert max(err.values()) <= 1e-3, err
+
+
+# ---------------------------------------------------------------------------
+def test_state_roundtrip_and_determinism(torch_mod, orc):
+    cfg = W.SMALL
+    xv, x, v, gB, p = oracle_state(orc, cfg, 0.2, 0.3, seed=3)
+    body = np.array([0.01, 0.0, 0.2, 0.0, 0.1, 0.3])
+    with _sim(cfg) as s:
+        s.set_state(xv, body)
+        a, b = s.state()
+        np.testing.assert_array_equal(a.cpu().numpy(), xv)
+        np.testing.assert_array_equal(b.cpu().numpy()[0], body)
+        s.step(57)
+        r1 = [t.cpu().numpy() for t in s.state()]
+        s.set_state(xv, body)
+        s.step(57)
+        r2 = [t.cpu().numpy() for t in s.state()]
+        s.check()
+    np.testing.assert_array_equal(r1[0], r2[0])
+    np.testing.assert_array_equal(r1[1], r2[1])
+
+
+def test_batch_equals_single_tanks(torch_mod, orc):
+    cfgs = [W.TINY, dict(W.SMALL, fill=0.3), dict(W.BASE, dx=0.015, fill=0.7)]
+    n = 64
+    us = [W.piecewise_profile(n, cfgs[0]["dt"], seed=40 + i, hold=(0.0005, 0.001)) for i in range(3)]
+    from paper_2604_12505_gb300.sph import Sim
+    singles = []
+    for c, u in zip(cfgs, us):
+        with Sim(c) as s:
+            y = s.step(n, u=u[None])
+            singles.append((y.cpu().numpy()[0], [t.cpu().numpy() for t in s.state()]))
+    with Sim(cfgs) as sb:
+        yb = sb.step(n, u=np.stack(us)).cpu().numpy()
+        xb, bb = [t.cpu().numpy() for t in sb.state()]
+        sb.check()
+        off = sb.offsets
+    for i in range(3):
+        np.testing.assert_array_equal(yb[i], singles[i][0])
+        np.testing.assert_array_equal(xb[off[i]:off[i + 1]], singles[i][1][0])
+        np.testing.assert_array_equal(bb[i], singles[i][1][1][0])
+
+
+def test_tile_shapes_agree_and_autotune_restores_state(torch_mod, orc):
+    cfg = W.SMALL
+    xv, x, v, gB, p = oracle_state(orc, cfg, 0.2, 0.3, seed=8)
+    ref = orc.evaluate(p, x, v, gB, np.zeros(6))
+    from paper_2604_12505_gb300.sph import Sim
+    with Sim(cfg) as s:
+        s.set_state(xv, np.zeros(6))
+        for code in range(1, 6):
+            s.set_tile(code)
+            out = s.eval()
+            assert normwise(out["acc"].cpu().numpy(), ref["acc"]) <= 1e-5
+        s.set_tile(3)
+        s.step(10)
+        before = [t.cpu().numpy() for t in s.state()]
+        chosen, us = s.autotune(steps=8)
+        after = [t.cpu().numpy() for t in s.state()]
+        assert 1 <= chosen <= 5 and all(t > 0 for t in us)
+        np.testing.assert_array_equal(before[0], after[0])
+        np.testing.assert_array_equal(before[1], after[1])
+        s.check()
+
+
+def test_health_flags_report_nan_and_escape(torch_mod, orc):
+    from paper_2604_12505_gb300 import _lib
+    from paper_2604_12505_gb300.sph import Sim
+    cfg = W.TINY
+    xv, *_ = oracle_state(orc, cfg)
+    with Sim(cfg) as s:
+        bad = xv.copy()
+        bad[3, 2] = np.nan
+        s.set_state(bad, np.zeros(6))
+        s.step(2)
+        f = s.check(raise_on_error=False, reset=True)
+        assert f & _lib.FLAG_NAN
+        bad = xv.copy()
+        bad[5, 0] = 10.0  # far outside the grid around the tank
+        s.set_state(bad, np.zeros(6))
+        s.step(1)
+        with pytest.raises(_lib.SphError) as ei:
+            s.check()
+        assert ei.value.code == -4
+        assert s.check(raise_on_error=False, reset=True) & _lib.FLAG_ESCAPED
+        s.set_state(xv, np.zeros(6))
+        s.step(3)
+        assert s.check() == 0
+
+
+def test_pair_count_matches_neighbour_counts(torch_mod, orc):
+    cfg = W.SMALL
+    xv, x, v, gB, p = oracle_state(orc, cfg, 0.1, 0.0, seed=2)
+    nff, nfg2, nfg1 = orc.neighbor_counts_f32(p, xv[:, :2], gB, np.zeros(6))
+    from paper_2604_12505_gb300.sph import Sim
+    with Sim(cfg) as s:
+        s.set_state(xv, np.zeros(6))
+        c0 = s.pair_count()
+        s.step(1)
+        assert s.pair_count() - c0 == int(nff.sum() + nfg1.sum())
+
+
+def test_relaxation_parity(torch_mod, orc):
+    # Damped relaxation with the tank held fixed (Section 5.1), 300 steps.
+    cfg = W.SMALL
+    xv, x, v, gB, p = oracle_state(orc, cfg)
+    body = np.array([0.0, 0.0, 0.1, 0.0, 0.0, 0.0])
+    xr, vr, br, _, _ = orc.run(p, x, v, gB, body, 300, damping=2e-3, record=False)
+    with _sim(cfg) as s:
+        s.set_state(xv, body)
+        s.relax(300, damping=2e-3)
+        s.check()
+        xg, bg = [t.cpu().numpy().astype(np.float64) for t in s.state()]
+    np.testing.assert_array_equal(bg[0], body)
+    np.testing.assert_array_equal(br, body)
+    disp = np.linalg.norm(xr - x, axis=1).max()
+    assert np.linalg.norm(xg[:, :2] - xr, axis=1).max() <= 1e-3 * disp
+    assert normwise(xg[:, 2:], vr) <= 1e-3
