@@ -128,6 +128,7 @@ struct sph_sim {
     RunDev* d_run = nullptr;
     int4* d_tiles[SPH_TILE_COUNT + 1] = {nullptr};
     int* d_tile_first[SPH_TILE_COUNT + 1] = {nullptr};
+    int* d_group_first[SPH_TILE_COUNT + 1] = {nullptr};
     int* d_part_tank = nullptr;
     double* d_scratch_body = nullptr;
     float* d_scratch_xv = nullptr;
@@ -142,6 +143,7 @@ struct sph_sim {
         SimDev s = S;
         s.tiles = d_tiles[tile_code];
         s.tile_tank_first = d_tile_first[tile_code];
+        s.group_first = d_group_first[tile_code];
         s.n_tiles = n_tiles[tile_code];
         return s;
     }
@@ -167,6 +169,7 @@ void free_sim(sph_sim* s)
     for (int c = 0; c <= SPH_TILE_COUNT; ++c) {
         cudaFree(s->d_tiles[c]);
         cudaFree(s->d_tile_first[c]);
+        cudaFree(s->d_group_first[c]);
     }
     cudaFree(s->d_part_tank);
     cudaFree(s->d_scratch_body);
@@ -178,6 +181,10 @@ void free_sim(sph_sim* s)
     }
     cudaFree(s->S.rhoP);
     cudaFree(s->S.partials);
+    cudaFree(s->S.gpartials);
+    cudaFree(s->S.nbl);
+    cudaFree(s->S.nbn);
+    cudaFree(s->S.gdone);
     cudaFree((void*)s->S.gB);
     cudaFree((void*)s->S.gstart);
     cudaFree(s->S.gpos);
@@ -301,9 +308,9 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
         return fail(SPH_E_UNSUPPORTED, "sph_create: more than 2^31 grid slots");
     }
     // tile tables for every shape
-    int max_tiles = 0;
+    int max_tiles = 0, max_groups = 0;
     std::vector<std::vector<int4>> tiles(SPH_TILE_COUNT + 1);
-    std::vector<std::vector<int>> first(SPH_TILE_COUNT + 1);
+    std::vector<std::vector<int>> first(SPH_TILE_COUNT + 1), gfirst(SPH_TILE_COUNT + 1);
     for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
         int TX, TY;
         tile_dims(code, &TX, &TY);
@@ -317,6 +324,13 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
         first[code].push_back((int)tiles[code].size());
         s->n_tiles[code] = (int)tiles[code].size();
         max_tiles = std::max(max_tiles, s->n_tiles[code]);
+        int ng = 0;
+        for (int b = 0; b < B; ++b) {
+            gfirst[code].push_back(ng);
+            ng += (first[code][b + 1] - first[code][b] + kTileGroup - 1) / kTileGroup;
+        }
+        gfirst[code].push_back(ng);
+        max_groups = std::max(max_groups, ng);
     }
     s->tile_code = 3;
 
@@ -328,6 +342,7 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
     for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
         rc |= dalloc(&s->d_tiles[code], tiles[code].size());
         rc |= dalloc(&s->d_tile_first[code], first[code].size());
+        rc |= dalloc(&s->d_group_first[code], gfirst[code].size());
     }
     rc |= dalloc(&s->d_part_tank, s->n_f_total);
     rc |= dalloc(&s->d_scratch_body, 6 * (size_t)B);
@@ -339,6 +354,19 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
     }
     rc |= dalloc(&s->S.rhoP, nslot);
     rc |= dalloc(&s->S.partials, max_tiles);
+    rc |= dalloc(&s->S.gpartials, max_groups);
+    {   // neighbour lists: per tile kNbrMax x (TX*TY*12) entries, sized for the largest shape
+        size_t nb = 0, nn = 0;
+        for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
+            int TX, TY;
+            tile_dims(code, &TX, &TY);
+            nn = std::max(nn, (size_t)s->n_tiles[code] * TX * TY * 12);
+        }
+        nb = nn * kNbrMax;
+        rc |= dalloc(&s->S.nbl, nb);
+        rc |= dalloc(&s->S.nbn, nn);
+    }
+    rc |= dalloc(&s->S.gdone, max_groups);
     float4* gB_d;
     int* gstart_d;
     rc |= dalloc(&gB_d, gB_sorted.size());
@@ -368,9 +396,11 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
     CKF(cudaMemcpy(s->d_tank, td.data(), B * sizeof(TankDev), cudaMemcpyHostToDevice));
     CKF(cudaMemset(s->d_body, 0, B * sizeof(BodyDev)));
     CKF(cudaMemset(s->d_run, 0, sizeof(RunDev)));
+    CKF(cudaMemset(s->S.gdone, 0, max_groups * sizeof(unsigned int)));
     for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
         CKF(cudaMemcpy(s->d_tiles[code], tiles[code].data(), tiles[code].size() * sizeof(int4), cudaMemcpyHostToDevice));
         CKF(cudaMemcpy(s->d_tile_first[code], first[code].data(), first[code].size() * sizeof(int), cudaMemcpyHostToDevice));
+        CKF(cudaMemcpy(s->d_group_first[code], gfirst[code].data(), gfirst[code].size() * sizeof(int), cudaMemcpyHostToDevice));
     }
     CKF(cudaMemcpy(s->d_part_tank, part_tank.data(), part_tank.size() * sizeof(int), cudaMemcpyHostToDevice));
     if (!gB_sorted.empty()) {

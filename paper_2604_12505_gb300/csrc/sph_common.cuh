@@ -60,7 +60,7 @@ struct BodyDev {
     float fo_next[2];             // fl32(r - W): origin of the grid the force pass bins into
     float2 dc, ds, drx, dry;      // cos, sin, r as two-float (hi, lo) splits of the FP64 values
     float fvx, fvy, fw;           // rdot, thetadot rounded to FP32
-    unsigned int done;            // tiles of this tank finished in the current force pass
+    unsigned int done;            // reduction groups of this tank finished in the current force pass
     int flags;                    // SPH_FLAG_* bits
 };
 
@@ -127,12 +127,18 @@ __device__ __forceinline__ F2 f2_add(F2 a, F2 b)
     return F2{hi, lo - (hi - s)};
 }
 
-struct TilePartial {
-    F2 fx, fy, t;                 // fluid force / torque on the body from this tile
-    float cx, cy;                 // sum of own particle positions (sample steps only)
-    int pairs;                    // pair interactions evaluated by this tile
-    int wall;                     // 1 if any ghost pair contributed
+// Partial sums of one tile (or of a group of kTileGroup tiles), read back
+// with three 16-byte loads:
+//   a = (F_x hi, F_x lo, F_y hi, F_y lo)   fluid force on the body
+//   b = (T hi, T lo, sum x hi, sum x lo)    torque; particle-position sum (sample steps)
+//   c = (sum y hi, sum y lo, pairs, wall)   as int bits; pair interactions; any ghost pair
+struct __align__(16) TilePartial {
+    float4 a, b;
+    int4 c;
 };
+
+constexpr int kTileGroup = 64;    // tiles per first-level reduction group
+constexpr int kNbrMax = 40;       // fluid neighbours recorded per particle by the density pass
 
 // Optional per-particle outputs of an evaluation pass (indexed by particle).
 struct EvalOut {
@@ -155,11 +161,16 @@ struct SimDev {
     float2* rhoP;                 // indexed by slot of the current buffer
     const int4* tiles;            // (tank, first cell x, first cell y, tile index within tank)
     const int* tile_tank_first;   // per tank: first tile (size B + 1)
-    TilePartial* partials;
+    const int* group_first;       // per tank: first reduction group (size B + 1)
+    TilePartial* partials;        // per tile
+    TilePartial* gpartials;       // per group of kTileGroup tiles
+    unsigned int* gdone;          // per group: tiles finished in the current force pass
     const float4* gB;             // body-frame ghost positions as two-float (x_hi, x_lo, y_hi, y_lo), sorted by ghost cell
     const int* gstart;            // per tank (G*G + 1) ghost-cell starts (global ghost index)
     float4* gpos;                 // per step: (hi_x, hi_y, lo_x, lo_y) world position, written by the density pass
     float4* gvel;                 // per step: (v_x, v_y, arm_x, arm_y)
+    unsigned short* nbl;          // per tile [kNbrMax][max own]: staged index of each fluid neighbour
+    unsigned char* nbn;           // per tile [max own]: neighbour count (> kNbrMax: not recorded)
     int B;
     int n_tiles;
 };

@@ -33,6 +33,7 @@ struct Shape {
     static constexpr int SY = TY + 2;
     static constexpr int NC = SX * SY;       // staged cells (tile + halo)
     static constexpr int MAXS = NC * 12;     // staged particles (1.8x the lattice mean)
+    static constexpr int MAXOWN = TX * TY * 12;  // own particles with a recorded neighbour list
     static constexpr int THREADS = (TX * TY >= 32) ? 256 : (TX * TY >= 16 ? 128 : (TX * TY >= 8 ? 64 : 32));
 };
 
@@ -203,6 +204,11 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
         const float4 pi = sm.pv[e];
         const int c = sm.cell[e];
         float Sf = 0.f, Df = 0.f;
+        // the fluid neighbours found here (staged index, r < 2h, j != i) are
+        // recorded for the force pass, which stages the tile identically
+        const bool rec = t < Sh::MAXOWN;
+        unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
+        int nn = 0;
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
             const int a = sm.start[c + dy * Sh::SX - 1], z = sm.start[c + dy * Sh::SX + 2];
@@ -214,11 +220,16 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
                     const float inv_r = rsqrtf(r2);
                     const float r = r2 * inv_r;
                     Sf += (r2 > 0.f) ? w_cubic(T, r) : T.cW * 4.0f;
-                    if (want_drho && j != e && r2 > 0.f)
-                        Df += ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * dw_cubic_over_r(T, r, inv_r);
+                    if (j != e) {
+                        if (rec && nn < kNbrMax) lst[nn * Sh::MAXOWN] = (unsigned short)j;
+                        ++nn;
+                        if (want_drho && r2 > 0.f)
+                            Df += ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * dw_cubic_over_r(T, r, inv_r);
+                    }
                 }
             }
         }
+        if (rec) S.nbn[blockIdx.x * Sh::MAXOWN + t] = (unsigned char)min(nn, 255);
         float Sg = 0.f, Dg = 0.f;
         int ng2 = 0;
         for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
@@ -309,33 +320,48 @@ __device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* >= 32 
     return r;
 }
 
+__device__ __forceinline__ void store_partial(TilePartial* P, const Red& r, int wall)
+{
+    P->a = make_float4(r.fx.hi, r.fx.lo, r.fy.hi, r.fy.lo);
+    P->b = make_float4(r.t.hi, r.t.lo, r.cx.hi, r.cx.lo);
+    P->c = make_int4(__float_as_int(r.cy.hi), __float_as_int(r.cy.lo), (int)r.pairs, wall);
+}
+
+// Block-wide sum of partials [p0, p1) in fixed order (result in thread 0);
+// *wall receives whether any of them saw a ghost pair (all threads).
+__device__ Red reduce_partials(const TilePartial* P, int p0, int p1, bool com, int* wall, Red* scratch)
+{
+    const F2 z{0.f, 0.f};
+    Red r{z, z, z, z, z, 0ull};
+    int w = 0;
+    for (int i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+        const float4 a = __ldcg(&P[i].a), b = __ldcg(&P[i].b);
+        const int4 c = __ldcg(&P[i].c);
+        r.fx = f2_add(r.fx, F2{a.x, a.y});
+        r.fy = f2_add(r.fy, F2{a.z, a.w});
+        r.t = f2_add(r.t, F2{b.x, b.y});
+        if (com) {
+            r.cx = f2_add(r.cx, F2{b.z, b.w});
+            r.cy = f2_add(r.cy, F2{__int_as_float(c.x), __int_as_float(c.y)});
+        }
+        r.pairs += (unsigned long long)(unsigned)c.z;
+        w |= c.w;
+    }
+    *wall = __syncthreads_or(w);
+    return block_reduce(r, true, com, scratch);
+}
+
 // ---------------------------------------------------------------------------
 // Body update by the last CTA of a tank (Eq. 20, Eq. 28, outputs)
 // ---------------------------------------------------------------------------
 __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
-                              Red* scratch)
+                              bool sample, Red* scratch)
 {
     __threadfence();
     RunDev* run = S.run;
     const long long step = run->step;
-    const bool sample = !eval && (step % T.outer_every) == 0;
-    const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
-    const F2 z{0.f, 0.f};
-    Red r{z, z, z, z, z, 0ull};
-    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) {
-        const TilePartial* P = S.partials + t;
-        if (__ldcg(&P->wall)) {
-            r.fx = f2_add(r.fx, F2{__ldcg(&P->fx.hi), __ldcg(&P->fx.lo)});
-            r.fy = f2_add(r.fy, F2{__ldcg(&P->fy.hi), __ldcg(&P->fy.lo)});
-            r.t = f2_add(r.t, F2{__ldcg(&P->t.hi), __ldcg(&P->t.lo)});
-        }
-        if (sample) {
-            r.cx = f2_add(r.cx, F2{__ldcg(&P->cx), 0.f});
-            r.cy = f2_add(r.cy, F2{__ldcg(&P->cy), 0.f});
-        }
-        r.pairs += (unsigned long long)__ldcg(&P->pairs);
-    }
-    r = block_reduce(r, true, sample, scratch);
+    int wall;
+    Red r = reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall, scratch);
     if (threadIdx.x != 0) return;
 
     // FP64 from here on: assembly of the reduced force/torque and the body
@@ -460,26 +486,39 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
             const int c = sm.cell[e];
             float ax = 0.f, ay = 0.f;
             int nff = 0;
+            // one fluid pair, r < 2h, j != i: Eqs. 10 and 12
+            auto pair = [&](int j) {
+                const float4 pj = sm.pv[j];
+                const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);
+                const float r2 = dist2(ddx, ddy);
+                if (r2 > 0.f) {
+                    const float2 rj = sm.rho[j];
+                    const float inv_r = rsqrtf(r2);
+                    const float r = r2 * inv_r;
+                    const float gW = dw_cubic_over_r(T, r, inv_r);
+                    const float press = -(ri.y + rj.y);                                  // Eq. 10
+                    const float vr = (pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy;
+                    const float visc = __fdividef(T.visc_a * vr, (ri.x + rj.x) * (r2 + T.epsh2));  // Eq. 12
+                    const float s = T.m * (press + visc) * gW;
+                    ax = fmaf(s, ddx, ax);
+                    ay = fmaf(s, ddy, ay);
+                }
+            };
+            const int nn = t < Sh::MAXOWN ? (int)S.nbn[blockIdx.x * Sh::MAXOWN + t] : 255;
+            if (nn <= kNbrMax) {  // the list recorded by the density pass (dense: no candidate tests)
+                const unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
+                nff = nn;
+#pragma unroll 4
+                for (int k = 0; k < nn; ++k) pair(lst[k * Sh::MAXOWN]);
+            } else {              // list overflow: scan the 3x3 cells
 #pragma unroll
-            for (int dy = -1; dy <= 1; ++dy) {
-                const int a = sm.start[c + dy * Sh::SX - 1], zz = sm.start[c + dy * Sh::SX + 2];
-                for (int j = a; j < zz; ++j) {
-                    const float4 pj = sm.pv[j];
-                    const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);
-                    const float r2 = dist2(ddx, ddy);
-                    if (r2 < T.R2 && j != e) {
-                        ++nff;
-                        if (r2 > 0.f) {
-                            const float2 rj = sm.rho[j];
-                            const float inv_r = rsqrtf(r2);
-                            const float r = r2 * inv_r;
-                            const float gW = dw_cubic_over_r(T, r, inv_r);
-                            const float press = -(ri.y + rj.y);                          // Eq. 10
-                            const float vr = (pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy;
-                            const float visc = __fdividef(T.visc_a * vr, (ri.x + rj.x) * (r2 + T.epsh2));  // Eq. 12
-                            const float s = T.m * (press + visc) * gW;
-                            ax = fmaf(s, ddx, ax);
-                            ay = fmaf(s, ddy, ay);
+                for (int dy = -1; dy <= 1; ++dy) {
+                    const int a = sm.start[c + dy * Sh::SX - 1], zz = sm.start[c + dy * Sh::SX + 2];
+                    for (int j = a; j < zz; ++j) {
+                        const float4 pj = sm.pv[j];
+                        if (j != e && dist2(__fsub_rn(pi.x, pj.x), __fsub_rn(pi.y, pj.y)) < T.R2) {
+                            ++nff;
+                            pair(j);
                         }
                     }
                 }
@@ -556,22 +595,31 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
     if (flags) atomicOr(&S.body[tank].flags, flags);
     const bool any_wall = __syncthreads_or(wall) != 0;
     Red r = block_reduce(acc, any_wall, sample, scratch);
+    // two-level fixed-order reduction: the last tile of a group of
+    // kTileGroup tiles sums the group, the last group of a tank finalizes it
+    const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
+    const int gi = (blockIdx.x - t0) / kTileGroup;
+    const int gt0 = t0 + gi * kTileGroup, gt1 = min(gt0 + kTileGroup, t1);
+    const int g = S.group_first[tank] + gi;
     if (threadIdx.x == 0) {
-        TilePartial P;
-        P.fx = r.fx;
-        P.fy = r.fy;
-        P.t = r.t;
-        P.cx = r.cx.hi + r.cx.lo;
-        P.cy = r.cy.hi + r.cy.lo;
-        P.pairs = (int)r.pairs;
-        P.wall = any_wall ? 1 : 0;
-        S.partials[blockIdx.x] = P;
+        store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
         __threadfence();
-        const unsigned n_tiles = (unsigned)(S.tile_tank_first[tank + 1] - S.tile_tank_first[tank]);
-        is_last = (atomicAdd(&S.body[tank].done, 1u) == n_tiles - 1);
+        is_last = (atomicAdd(&S.gdone[g], 1u) == (unsigned)(gt1 - gt0 - 1));
     }
     __syncthreads();
-    if (is_last) tank_finalize(S, T, tank, eval, E, nbuf, scratch);
+    if (!is_last) return;
+    __threadfence();
+    int wall_g;
+    r = reduce_partials(S.partials, gt0, gt1, sample, &wall_g, scratch);
+    if (threadIdx.x == 0) {
+        store_partial(S.gpartials + g, r, wall_g);
+        S.gdone[g] = 0;
+        __threadfence();
+        const unsigned n_groups = (unsigned)(S.group_first[tank + 1] - S.group_first[tank]);
+        is_last = (atomicAdd(&S.body[tank].done, 1u) == n_groups - 1);
+    }
+    __syncthreads();
+    if (is_last) tank_finalize(S, T, tank, eval, E, nbuf, sample, scratch);
 }
 
 // ---------------------------------------------------------------------------
