@@ -237,6 +237,33 @@ int sph_time_kernels(sph_sim* sim, int32_t n_steps, double* us, void* stream);
 int sph_run_batch(const sph_params* p, int32_t B, const double* u_profiles, int32_t T, const sph_ctrl* pd,
                   double* y_out, int32_t* n_particles_out, void* stream);
 
+/*
+ * Density without any memory allocation.  The paper has no counterpart: this
+ * call exists for callers that cannot call cudaMalloc, such as software that
+ * must fix its device memory before it starts running (flight or real-time
+ * loops) or a plugin inside an application that owns all device memory.
+ *
+ * Computes the ghost-corrected density of Eq. 14 (self term included, the
+ * neighbour search of sph_eval) for a state the caller passes in:
+ *  p       host tank parameters (geometry, h, rho0, gamma1, sigma_cubic)
+ *  xv      device float32 [n_fluid, 4] fluid rows (x, y, vx, vy), world frame
+ *  gB      device float64 [n_ghost, 2] ghost positions in the body frame
+ *  body    HOST float64 [6] body state (r_x, r_y, theta, ...)
+ *  rho     device float32 [n_fluid] output
+ * Its working memory is one fixed device array inside the library (about
+ * 8.6 MB, created when the library loads, kept by every GPU that loads the
+ * library until the process exits): at most 256 x 256 neighbour-grid cells
+ * (set by R / dx), 16384 ghosts and 32 particles per cell.  Larger requests
+ * return SPH_E_UNSUPPORTED with a message, and a crowded cell returns
+ * SPH_E_DIVERGED.  The first call on a device looks up the array's device
+ * address, so make that first call before any stream capture.  Every call
+ * reuses the same array, so calls must not overlap on the GPU: two calls
+ * issued on different streams or from different threads at the same time
+ * race.  Blocks until the stream has finished the call.
+ */
+int sph_density_noalloc(const sph_params* p, const float* xv, int32_t n_fluid, const double* gB, int32_t n_ghost,
+                        const double* body, float* rho, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -76,6 +76,7 @@ def _declare(L):
         "sph_relax": ([vp, i32, C.c_double, vp], C.c_int),
         "sph_time_kernels": ([vp, i32, dp, vp], C.c_int),
         "sph_run_batch": ([P, i32, vp, i32, C.POINTER(SphCtrl), vp, ip, vp], C.c_int),
+        "sph_density_noalloc": ([P, vp, i32, vp, i32, dp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

@@ -115,6 +115,11 @@ int dalloc(T** p, size_t n)
 
 }  // namespace
 
+namespace sph {
+// Lets other translation units of the library set the last-error text.
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace sph
+
 struct sph_sim {
     int B = 0;
     std::vector<TankHost> tanks;
