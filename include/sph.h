@@ -208,6 +208,27 @@ int sph_check(sph_sim* sim, int32_t* flags, int32_t reset, void* stream);
 int sph_pair_count(sph_sim* sim, int64_t* pairs, void* stream);
 
 /*
+ * Forward-mode derivative (JVP) of K inner steps: the linearization of the
+ * state transition of Algorithm 1 plus symplectic Euler along the
+ * trajectory it computes (Section 3.5: Jacobians of the simulator).  The
+ * primal state advances by K steps exactly as sph_step would with input u
+ * (no controller), and a tangent is carried alongside it; the neighbour set
+ * of each step is the one the primal uses.
+ *  u        float64 [B, K, 3] input (NULL: zero)
+ *  du       float64 [B, K, 3] tangent of the input (NULL: zero)
+ *  dxv0     float32 [N, 4] tangent of the fluid state (x, y, vx, vy) (NULL: zero)
+ *  dbody0   float64 [B, 6] tangent of the body state (NULL: zero)
+ *  y_out    float64 [B, n_samples, SPH_NY] primal samples, as sph_step (NULL: none)
+ *  dy_out   float64 [B, n_samples, SPH_NY] tangent of the samples (NULL: none)
+ *  dxv_out  float32 [N, 4] tangent of the final fluid state (NULL: none)
+ *  dbody_out float64 [B, 6] tangent of the final body state (NULL: none)
+ * Tangent kernels exist for tile shapes up to 8x4; a larger chosen shape is
+ * replaced by 8x4 for this call.  Allocates the tangent buffers on first use.
+ */
+int sph_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv0, const double* dbody0, int32_t K,
+            double* y_out, double* dy_out, float* dxv_out, double* dbody_out, void* stream);
+
+/*
  * Kernel-shape control.  tile = 0 lets the library pick; otherwise one of
  * the codes 1..SPH_TILE_COUNT (cell blocks 2x2, 4x2, 4x4, 8x4, 8x8).
  * sph_autotune times every shape on the current state for `steps` steps,

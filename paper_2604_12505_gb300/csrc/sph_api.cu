@@ -142,14 +142,16 @@ struct sph_sim {
     cudaGraphExec_t graph = nullptr;
     int graph_tile = 0;
     bool use_pdl = true;
+    int max_tiles = 0, max_groups = 0;
 
-    SimDev dev() const
+    SimDev dev(int code = 0) const
     {
+        if (code == 0) code = tile_code;
         SimDev s = S;
-        s.tiles = d_tiles[tile_code];
-        s.tile_tank_first = d_tile_first[tile_code];
-        s.group_first = d_group_first[tile_code];
-        s.n_tiles = n_tiles[tile_code];
+        s.tiles = d_tiles[code];
+        s.tile_tank_first = d_tile_first[code];
+        s.group_first = d_group_first[code];
+        s.n_tiles = n_tiles[code];
         return s;
     }
 
@@ -189,6 +191,11 @@ void free_sim(sph_sim* s)
     cudaFree(s->S.gpartials);
     cudaFree(s->S.nbl);
     cudaFree(s->S.nbn);
+    for (int b = 0; b < 2; ++b) cudaFree(s->S.tpv[b]);
+    cudaFree(s->S.trho);
+    cudaFree(s->S.tgh);
+    cudaFree(s->S.tpartials);
+    cudaFree(s->S.tgpartials);
     cudaFree(s->S.gdone);
     cudaFree((void*)s->S.gB);
     cudaFree((void*)s->S.gstart);
@@ -358,6 +365,8 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
         rc |= dalloc(&s->S.count[b], s->n_cells_total);
     }
     rc |= dalloc(&s->S.rhoP, nslot);
+    s->max_tiles = max_tiles;
+    s->max_groups = max_groups;
     rc |= dalloc(&s->S.partials, max_tiles);
     rc |= dalloc(&s->S.gpartials, max_groups);
     {   // neighbour lists: per tile kNbrMax x (TX*TY*12) entries, sized for the largest shape
@@ -578,6 +587,51 @@ int sph_relax(sph_sim* sim, int32_t n_steps, double damping, void* stream)
         if (rc) return rc;
     }
     sim->host_step += n_steps;
+    return SPH_OK;
+}
+
+int sph_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv0, const double* dbody0, int32_t K,
+            double* y_out, double* dy_out, float* dxv_out, double* dbody_out, void* stream)
+{
+    if (!sim || K < 0) return fail(SPH_E_INVAL, "sph_jvp: bad argument");
+    for (int b = 1; b < sim->B; ++b)
+        if (sim->tanks[b].p.outer_every != sim->tanks[0].p.outer_every)
+            return fail(SPH_E_UNSUPPORTED, "sph_jvp: tanks of a batch must share outer_every");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!sim->S.trho) {  // tangent buffers, allocated on first use
+        const size_t nslot = (size_t)sim->n_cells_total * kCap;
+        int rc = SPH_OK;
+        for (int b = 0; b < 2; ++b) rc |= dalloc(&sim->S.tpv[b], nslot);
+        rc |= dalloc(&sim->S.trho, nslot);
+        rc |= dalloc(&sim->S.tgh, sim->n_g_total);
+        rc |= dalloc(&sim->S.tpartials, sim->max_tiles);
+        rc |= dalloc(&sim->S.tgpartials, sim->max_groups);
+        if (rc) return SPH_E_NOMEM;
+    }
+    const int code = sim->tile_code > 4 ? 4 : sim->tile_code;  // tangent kernels exist for tiles up to 8x4
+    const SimDev S = sim->dev(code);
+    const int buf = (int)(sim->host_step & 1);
+    CK(launch_tangent_state(S, dxv0, nullptr, dbody0, nullptr, sim->n_cells_total, buf, st));
+    int32_t ns = 0;
+    sph_samples_for(sim, K, &ns);
+    RunDev d{};
+    d.u = u;
+    d.du = du;
+    d.u_tank_stride = 3ll * K;
+    d.y = y_out;
+    d.dy = dy_out;
+    d.y_tank_stride = (long long)ns * SPH_NY;
+    CK(launch_set_run(sim->d_run, d, st));
+    EvalOut E{};
+    for (int i = 0; i < K; ++i) {
+        cudaError_t e = launch_step(S, E, 0, code, sim->n_tiles[code], st, sim->use_pdl, true);
+        if (e != cudaSuccess) return fail(SPH_E_CUDA, std::string("sph_jvp launch: ") + cudaGetErrorString(e));
+    }
+    sim->host_step += K;
+    if (dxv_out || dbody_out) {
+        float* tx = dxv_out ? dxv_out : sim->d_scratch_xv;
+        CK(launch_tangent_state(S, nullptr, tx, nullptr, dbody_out, sim->n_cells_total, (int)(sim->host_step & 1), st));
+    }
     return SPH_OK;
 }
 

@@ -60,6 +60,9 @@ struct BodyDev {
     float fo_next[2];             // fl32(r - W): origin of the grid the force pass bins into
     float2 dc, ds, drx, dry;      // cos, sin, r as two-float (hi, lo) splits of the FP64 values
     float fvx, fvy, fw;           // rdot, thetadot rounded to FP32
+    // tangent (forward-mode derivative) of the body state, FP64, and its FP32 copy
+    double tr[2], tth, tv[2], tw;
+    float ftr[2], ftth, ftv[2], ftw;
     unsigned int done;            // reduction groups of this tank finished in the current force pass
     int flags;                    // SPH_FLAG_* bits
 };
@@ -108,6 +111,8 @@ struct RunDev {
     int ctrl_on;
     float damping;                // relaxation: v <- (1 - damping) v after the kick (0: physical model)
     int body_fixed;               // relaxation: the tank is held at its pose
+    const double* du;             // tangent of the input, [B, n_rows, 3] (NULL: 0)
+    double* dy;                   // tangent samples [B, n_samples, SPH_NY] (NULL: none)
     unsigned int tanks_done;      // tanks finished in the current force pass
 };
 
@@ -171,6 +176,12 @@ struct SimDev {
     float4* gvel;                 // per step: (v_x, v_y, arm_x, arm_y)
     unsigned short* nbl;          // per tile [kNbrMax][max own]: staged index of each fluid neighbour
     unsigned char* nbn;           // per tile [max own]: neighbour count (> kNbrMax: not recorded)
+    // forward-mode tangent (JVP) state, allocated on first use
+    float4* tpv[2];               // per slot (dx, dy, dvx, dvy), binned with the primal
+    float2* trho;                 // per slot (d rho, d(P / rho^2))
+    float4* tgh;                  // per ghost (d r_g, d v_g)
+    TilePartial* tpartials;       // tangent partials per tile / group
+    TilePartial* tgpartials;
     int B;
     int n_tiles;
 };
@@ -197,6 +208,15 @@ __device__ __forceinline__ float dw_cubic_over_r(const TankDev& T, float r, floa
     float fp = -3.0f * a * a;
     if (q < 1.0f) fp += 12.0f * b * b;
     return T.cdW * fp * inv_r;
+}
+
+// d/dr of (dW/dr)/r for the cubic spline, given G = (dW/dr)/r: (W'' - G) / r.
+__device__ __forceinline__ float dG_cubic_dr(const TankDev& T, float r, float inv_r, float G)
+{
+    float q = r * T.inv_h;
+    float fpp = 6.0f * (2.0f - q);
+    if (q < 1.0f) fpp -= 24.0f * (1.0f - q);
+    return (T.cdW * T.inv_h * fpp - G) * inv_r;
 }
 
 // Squared distance with the exact operation sequence of the integer decisions:

@@ -43,7 +43,7 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 // ---------------------------------------------------------------------------
 // Shared-memory staging of a tile and its halo
 // ---------------------------------------------------------------------------
-template <int TX, int TY, bool RHO>
+template <int TX, int TY, bool RHO, bool TAN = false>
 struct Stage {
     using Sh = Shape<TX, TY>;
     int start[Sh::NC + 1];
@@ -54,13 +54,15 @@ struct Stage {
     int slot[Sh::MAXS];
     unsigned char cell[Sh::MAXS];
     float2 rho[RHO ? Sh::MAXS : 1];
+    float4 tpv[TAN ? Sh::MAXS : 1];           // tangent (dx, dy, dvx, dvy)
+    float2 trho[(TAN && RHO) ? Sh::MAXS : 1];  // tangent (d rho, d(P / rho^2))
 };
 
 // Loads the counts, scans them, and gathers the particles of the (TX+2) x
 // (TY+2) staged cells, each cell ordered by particle index.  Returns false
 // (uniformly over the block) if the staged set does not fit.
-template <int TX, int TY, bool RHO>
-__device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, int cy0, Stage<TX, TY, RHO>& sm)
+template <int TX, int TY, bool RHO, bool TAN>
+__device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, int cy0, Stage<TX, TY, RHO, TAN>& sm)
 {
     using Sh = Shape<TX, TY>;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -130,6 +132,10 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
         const int gs = (T.cell_base + iy * T.G + ix) * kCap + (e - a);
         sm.pv[d] = S.pv[buf][gs];
         if (RHO) sm.rho[d] = S.rhoP[gs];
+        if constexpr (TAN) {
+            sm.tpv[d] = S.tpv[buf][gs];
+            if (RHO) sm.trho[d] = S.trho[gs];
+        }
         sm.pid[d] = id;
         sm.slot[d] = gs;
     }
@@ -138,8 +144,8 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
 }
 
 // Smem index of the t-th own particle (own cells are TY contiguous row runs).
-template <int TX, int TY, bool RHO>
-__device__ __forceinline__ int own_index(int t, const Stage<TX, TY, RHO>& sm)
+template <int TX, int TY, bool RHO, bool TAN>
+__device__ __forceinline__ int own_index(int t, const Stage<TX, TY, RHO, TAN>& sm)
 {
     using Sh = Shape<TX, TY>;
     int r = 0;
@@ -172,11 +178,13 @@ __device__ __forceinline__ void for_ghosts(const SimDev& S, const TankDev& T, fl
 // ---------------------------------------------------------------------------
 // Density pass: Eqs. 14, 11 (+ continuity sum)
 // ---------------------------------------------------------------------------
-template <int TX, int TY>
+// TAN: also the forward-mode tangent d rho (Eq. 14 differentiated along the
+// tangent of positions and of the body pose) and d(P / rho^2).
+template <int TX, int TY, bool TAN>
 __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev S, EvalOut E, int eval)
 {
     using Sh = Shape<TX, TY>;
-    __shared__ Stage<TX, TY, false> sm;
+    __shared__ Stage<TX, TY, false, TAN> sm;
     pdl_trigger();
     const int4 td = S.tiles[blockIdx.x];
     const TankDev& T = S.tank[td.x];
@@ -189,7 +197,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
         int ix = cx0 + c % TX, iy = cy0 + c / TX;
         if (ix < T.G && iy < T.G) S.count[nbuf][T.cell_base + iy * T.G + ix] = 0;
     }
-    if (!stage_tile<TX, TY, false>(S, T, buf, cx0, cy0, sm)) return;
+    if (!stage_tile<TX, TY, false, TAN>(S, T, buf, cx0, cy0, sm)) return;
     const int n_own = sm.own_row[TY];
     if (n_own == 0) return;
 
@@ -198,12 +206,23 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
     const float2 dc = b.dc, ds = b.ds, drx = b.drx, dry = b.dry;
     const float fvx = b.fvx, fvy = b.fvy, fw = b.fw;
     const bool want_drho = eval && E.drho;
+    float t_rx = 0.f, t_ry = 0.f, t_th = 0.f, t_vx = 0.f, t_vy = 0.f, t_w = 0.f;
+    if constexpr (TAN) {
+        t_rx = b.ftr[0];
+        t_ry = b.ftr[1];
+        t_th = b.ftth;
+        t_vx = b.ftv[0];
+        t_vy = b.ftv[1];
+        t_w = b.ftw;
+    }
 
     for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
         const int e = own_index(t, sm);
         const float4 pi = sm.pv[e];
         const int c = sm.cell[e];
-        float Sf = 0.f, Df = 0.f;
+        float Sf = 0.f, Df = 0.f, dRf = 0.f, dRg = 0.f;
+        float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (TAN) ti = sm.tpv[e];
         // the fluid neighbours found here (staged index, r < 2h, j != i) are
         // recorded for the force pass, which stages the tile identically
         const bool rec = t < Sh::MAXOWN;
@@ -225,6 +244,12 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
                         ++nn;
                         if (want_drho && r2 > 0.f)
                             Df += ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * dw_cubic_over_r(T, r, inv_r);
+                        if constexpr (TAN) {
+                            if (r2 > 0.f) {
+                                const float4 tj = sm.tpv[j];
+                                dRf += (ddx * (ti.x - tj.x) + ddy * (ti.y - tj.y)) * dw_cubic_over_r(T, r, inv_r);
+                            }
+                        }
                     }
                 }
             }
@@ -245,6 +270,13 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
             const float vgx = fvx - fw * army, vgy = fvy + fw * armx;
             S.gpos[g] = make_float4(gx.x, gy.x, gx.y, gy.y);
             S.gvel[g] = make_float4(vgx, vgy, armx, army);
+            float tgx = 0.f, tgy = 0.f;
+            if constexpr (TAN) {  // d r_g = d r + d theta z x arm, d v_g likewise (Eq. 21)
+                tgx = t_rx - t_th * army;
+                tgy = t_ry + t_th * armx;
+                S.tgh[g] = make_float4(tgx, tgy, t_vx - t_w * army - fw * t_th * armx,
+                                       t_vy + t_w * armx - fw * t_th * army);
+            }
             const float ddx = __fsub_rn(__fsub_rn(pi.x, gx.x), gx.y);
             const float ddy = __fsub_rn(__fsub_rn(pi.y, gy.x), gy.y);
             const float r2 = dist2(ddx, ddy);
@@ -255,11 +287,19 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
                 Sg += (r2 > 0.f) ? w_cubic(T, r) : T.cW * 4.0f;
                 if (want_drho && r2 > 0.f)
                     Dg += ((pi.z - vgx) * ddx + (pi.w - vgy) * ddy) * dw_cubic_over_r(T, r, inv_r);
+                if constexpr (TAN) {
+                    if (r2 > 0.f) dRg += (ddx * (ti.x - tgx) + ddy * (ti.y - tgy)) * dw_cubic_over_r(T, r, inv_r);
+                }
             }
         });
         const float rho = T.m * (Sf + T.gamma1 * Sg);          // Eq. 14
         const float P = T.k * (rho - T.rho0);                  // Eq. 11
-        S.rhoP[sm.slot[e]] = make_float2(rho, P / (rho * rho));
+        const float pr2 = P / (rho * rho);
+        S.rhoP[sm.slot[e]] = make_float2(rho, pr2);
+        if constexpr (TAN) {  // d rho, and d(P/rho^2) = d rho (k / rho^2 - 2 P / rho^3)
+            const float trh = T.m * (dRf + T.gamma1 * dRg);
+            S.trho[sm.slot[e]] = make_float2(trh, trh * (T.k / (rho * rho) - 2.0f * pr2 / rho));
+        }
         if (eval) {
             const int id = sm.pid[e];
             if (E.rho) E.rho[id] = rho;
@@ -355,13 +395,15 @@ __device__ Red reduce_partials(const TilePartial* P, int p0, int p1, bool com, i
 // Body update by the last CTA of a tank (Eq. 20, Eq. 28, outputs)
 // ---------------------------------------------------------------------------
 __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
-                              bool sample, Red* scratch)
+                              bool sample, bool tan, Red* scratch)
 {
     __threadfence();
     RunDev* run = S.run;
     const long long step = run->step;
     int wall;
     Red r = reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall, scratch);
+    Red tr = r;
+    if (tan) tr = reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall, scratch);
     if (threadIdx.x != 0) return;
 
     // FP64 from here on: assembly of the reduced force/torque and the body
@@ -399,6 +441,48 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
             y[9] = T.n_f ? ((double)r.cx.hi + (double)r.cx.lo) / T.n_f : 0.0;
             y[10] = T.n_f ? ((double)r.cy.hi + (double)r.cy.lo) / T.n_f : 0.0;
         }
+    }
+    if (tan && !eval) {  // tangent of Eq. 20 and of the kick-then-drift body step
+        const double dFx = (double)tr.fx.hi + (double)tr.fx.lo;
+        const double dFy = (double)tr.fy.hi + (double)tr.fy.lo;
+        const double dTq = (double)tr.t.hi + (double)tr.t.lo;
+        double dux = 0.0, duy = 0.0, dut = 0.0;
+        if (run->du) {
+            const double* du = run->du + tank * run->u_tank_stride + 3 * k;
+            dux = du[0];
+            duy = du[1];
+            dut = du[2];
+        }
+        if (sample && run->dy) {
+            const long long oe = T.outer_every;
+            const long long row = step / oe - (run->step0 + oe - 1) / oe;
+            double* y = run->dy + tank * run->y_tank_stride + row * SPH_NY;
+            y[0] = b.tr[0];
+            y[1] = b.tr[1];
+            y[2] = b.tth;
+            y[3] = b.tv[0];
+            y[4] = b.tv[1];
+            y[5] = b.tw;
+            y[6] = dFx;
+            y[7] = dFy;
+            y[8] = dTq;
+            y[9] = T.n_f ? ((double)tr.cx.hi + (double)tr.cx.lo) / T.n_f : 0.0;
+            y[10] = T.n_f ? ((double)tr.cy.hi + (double)tr.cy.lo) / T.n_f : 0.0;
+        }
+        if (!run->body_fixed) {
+            b.tv[0] += T.dt_d * (dFx + dux) / T.m_body;
+            b.tv[1] += T.dt_d * (dFy + duy) / T.m_body;
+            b.tw += T.dt_d * (dTq + dut) / T.J_body;
+            b.tr[0] += T.dt_d * b.tv[0];
+            b.tr[1] += T.dt_d * b.tv[1];
+            b.tth += T.dt_d * b.tw;
+        }
+        b.ftr[0] = (float)b.tr[0];
+        b.ftr[1] = (float)b.tr[1];
+        b.ftth = (float)b.tth;
+        b.ftv[0] = (float)b.tv[0];
+        b.ftv[1] = (float)b.tv[1];
+        b.ftw = (float)b.tw;
     }
     const double tau = ut + (run->ctrl_on ? b.tau_c : 0.0);
     const double ax = (Fx + ux) / T.m_body, ay = (Fy + uy) / T.m_body, aw = (Tq + tau) / T.J_body;
@@ -451,11 +535,13 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
 // ---------------------------------------------------------------------------
 // Force pass: Eqs. 10, 12, 16-19, Algorithm 1, symplectic Euler, re-binning
 // ---------------------------------------------------------------------------
-template <int TX, int TY>
+// TAN: also the forward-mode tangent of the accelerations, of the step and of
+// the body force/torque, along the tangent staged with the particles.
+template <int TX, int TY, bool TAN>
 __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S, EvalOut E, int eval)
 {
     using Sh = Shape<TX, TY>;
-    __shared__ Stage<TX, TY, true> sm;
+    __shared__ Stage<TX, TY, true, TAN> sm;
     __shared__ Red scratch[32];
     __shared__ int is_last;
     pdl_trigger();
@@ -471,20 +557,29 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
 
     const F2 z{0.f, 0.f};
     Red acc{z, z, z, z, z, 0ull};
+    Red tacc{z, z, z, z, z, 0ull};
     int flags = 0, wall = 0;
-    if (stage_tile<TX, TY, true>(S, T, buf, cx0, cy0, sm)) {
+    if (stage_tile<TX, TY, true, TAN>(S, T, buf, cx0, cy0, sm)) {
         const BodyDev& b = S.body[tank];
         const float bc = b.fc, bs = b.fs, brx = b.frx, bry = b.fry;
         const float ox = b.fo_next[0], oy = b.fo_next[1];  // origin of the next grid
         const int n_own = sm.own_row[TY];
         const float mm = T.m * T.m;
         float wfx = 0.f, wfy = 0.f, wt = 0.f, cxs = 0.f, cys = 0.f;
+        float twfx = 0.f, twfy = 0.f, twt = 0.f, tcxs = 0.f, tcys = 0.f;
+        const float t_th = TAN ? b.ftth : 0.f;
         for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
             const int e = own_index(t, sm);
             const float4 pi = sm.pv[e];
             const float2 ri = sm.rho[e];
             const int c = sm.cell[e];
-            float ax = 0.f, ay = 0.f;
+            float ax = 0.f, ay = 0.f, tax = 0.f, tay = 0.f;
+            float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
+            float2 tri = make_float2(0.f, 0.f);
+            if constexpr (TAN) {
+                ti = sm.tpv[e];
+                tri = sm.trho[e];
+            }
             int nff = 0;
             // one fluid pair, r < 2h, j != i: Eqs. 10 and 12
             auto pair = [&](int j) {
@@ -502,6 +597,21 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
                     const float s = T.m * (press + visc) * gW;
                     ax = fmaf(s, ddx, ax);
                     ay = fmaf(s, ddy, ay);
+                    if constexpr (TAN) {  // d(s d) = ds d + s dd
+                        const float4 tj = sm.tpv[j];
+                        const float2 trj = sm.trho[j];
+                        const float tdx = ti.x - tj.x, tdy = ti.y - tj.y;
+                        const float rd = ddx * tdx + ddy * tdy;                          // d . dd
+                        const float tG = dG_cubic_dr(T, r, inv_r, gW) * rd * inv_r;
+                        const float B = ri.x + rj.x, Cc = r2 + T.epsh2;
+                        const float tA = (ti.z - tj.z) * ddx + (ti.w - tj.w) * ddy + (pi.z - pj.z) * tdx +
+                                         (pi.w - pj.w) * tdy;
+                        const float tvisc = __fdividef(T.visc_a, B * Cc) *
+                                            (tA - vr * (__fdividef(tri.x + trj.x, B) + __fdividef(2.0f * rd, Cc)));
+                        const float ts = T.m * ((-(tri.y + trj.y) + tvisc) * gW + (press + visc) * tG);
+                        tax += ts * ddx + s * tdx;
+                        tay += ts * ddy + s * tdy;
+                    }
                 }
             };
             const int nn = t < Sh::MAXOWN ? (int)S.nbn[blockIdx.x * Sh::MAXOWN + t] : 255;
@@ -547,6 +657,31 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
                         wfx -= fx;                                                       // Eqs. 17, 19
                         wfy -= fy;
                         wt -= gv.z * fy - gv.w * fx;                                     // Eq. 20 torque
+                        if constexpr (TAN) {
+                            const float4 tg = __ldg(S.tgh + g);                           // (d r_g, d v_g)
+                            const float tdx = ti.x - tg.x, tdy = ti.y - tg.y;
+                            const float rd = ddx * tdx + ddy * tdy;
+                            const float tGs = -T.cdS * d * (T.h + r) * inv_r * inv_r * rd * inv_r;  // d(Gs)
+                            const float tfp = T.gp_sign * 2.0f * mm * tri.y;
+                            float tcv = 0.f;
+                            if (vr < 0.f) {
+                                const float Cc = r2 + T.epsh2;
+                                const float tA = (ti.z - tg.z) * ddx + (ti.w - tg.w) * ddy + (pi.z - gv.x) * tdx +
+                                                 (pi.w - gv.y) * tdy;
+                                tcv = __fdividef(mm * T.beta2, (ri.x + ri.x) * Cc) *
+                                      (tA - vr * (__fdividef(tri.x, ri.x) + __fdividef(2.0f * rd, Cc)));
+                            }
+                            const float cf = T.gp_sign * 2.0f * mm * ri.y +               // fp + fv without Gs
+                                             __fdividef(mm * T.beta2 * fminf(vr, 0.f), (ri.x + ri.x) * (r2 + T.epsh2));
+                            const float tf = (tfp + tcv) * gWs + cf * tGs;
+                            const float tfx = tf * ddx + f * tdx, tfy = tf * ddy + f * tdy;
+                            tax = fmaf(tfx, T.inv_m, tax);
+                            tay = fmaf(tfy, T.inv_m, tay);
+                            twfx -= tfx;
+                            twfy -= tfy;
+                            // d(arm x f) with d arm = d theta z x arm
+                            twt -= (-t_th * gv.w) * fy + gv.z * tfy - ((t_th * gv.z) * fx + gv.w * tfx);
+                        }
                     }
                 }
             });
@@ -554,6 +689,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
             acc.pairs += (unsigned long long)(nff + nfg);
             cxs += pi.x;
             cys += pi.y;
+            tcxs += ti.x;
+            tcys += ti.y;
             ax += T.grav_x;
             ay += T.grav_y;
             const int id = sm.pid[e];
@@ -581,6 +718,11 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
                 if (slot < kCap) {
                     S.pv[nbuf][cell * kCap + slot] = make_float4(x, y, vx, vy);
                     S.pid[nbuf][cell * kCap + slot] = id;
+                    if constexpr (TAN) {  // tangent of kick then drift, binned with the particle
+                        const float tvx = fmaf(T.dt, tax, ti.z) * damp, tvy = fmaf(T.dt, tay, ti.w) * damp;
+                        S.tpv[nbuf][cell * kCap + slot] = make_float4(fmaf(T.dt, tvx, ti.x), fmaf(T.dt, tvy, ti.y),
+                                                                      tvx, tvy);
+                    }
                 } else {
                     flags |= SPH_FLAG_CELL_FULL;
                 }
@@ -591,10 +733,17 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
         acc.t = F2{wt, 0.f};
         acc.cx = F2{cxs, 0.f};
         acc.cy = F2{cys, 0.f};
+        tacc.fx = F2{twfx, 0.f};
+        tacc.fy = F2{twfy, 0.f};
+        tacc.t = F2{twt, 0.f};
+        tacc.cx = F2{tcxs, 0.f};
+        tacc.cy = F2{tcys, 0.f};
     }
     if (flags) atomicOr(&S.body[tank].flags, flags);
     const bool any_wall = __syncthreads_or(wall) != 0;
     Red r = block_reduce(acc, any_wall, sample, scratch);
+    Red tr = r;
+    if constexpr (TAN) tr = block_reduce(tacc, any_wall, sample, scratch);
     // two-level fixed-order reduction: the last tile of a group of
     // kTileGroup tiles sums the group, the last group of a tank finalizes it
     const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
@@ -603,6 +752,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
     const int g = S.group_first[tank] + gi;
     if (threadIdx.x == 0) {
         store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
+        if constexpr (TAN) store_partial(S.tpartials + blockIdx.x, tr, any_wall ? 1 : 0);
         __threadfence();
         is_last = (atomicAdd(&S.gdone[g], 1u) == (unsigned)(gt1 - gt0 - 1));
     }
@@ -611,15 +761,17 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
     __threadfence();
     int wall_g;
     r = reduce_partials(S.partials, gt0, gt1, sample, &wall_g, scratch);
+    if constexpr (TAN) tr = reduce_partials(S.tpartials, gt0, gt1, sample, &wall_g, scratch);
     if (threadIdx.x == 0) {
         store_partial(S.gpartials + g, r, wall_g);
+        if constexpr (TAN) store_partial(S.tgpartials + g, tr, wall_g);
         S.gdone[g] = 0;
         __threadfence();
         const unsigned n_groups = (unsigned)(S.group_first[tank + 1] - S.group_first[tank]);
         is_last = (atomicAdd(&S.body[tank].done, 1u) == n_groups - 1);
     }
     __syncthreads();
-    if (is_last) tank_finalize(S, T, tank, eval, E, nbuf, sample, scratch);
+    if (is_last) tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN, scratch);
 }
 
 // ---------------------------------------------------------------------------
@@ -714,6 +866,63 @@ __global__ void gather_state_kernel(SimDev S, float4* __restrict__ xv, int n_cel
     }
 }
 
+// Tangent state transfer: one warp per cell; a particle's tangent lives in
+// the slot of the particle itself.  xv == NULL sets a zero tangent.
+__global__ void scatter_tangent_kernel(SimDev S, const float4* __restrict__ txv, int n_cells_total, int buf)
+{
+    const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (cell >= n_cells_total) return;
+    const int n = min(S.count[buf][cell], kCap);
+    if (lane < n) {
+        const int gs = cell * kCap + lane;
+        S.tpv[buf][gs] = txv ? txv[S.pid[buf][gs]] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+__global__ void gather_tangent_kernel(SimDev S, float4* __restrict__ txv, int n_cells_total, int buf)
+{
+    const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (cell >= n_cells_total) return;
+    const int n = min(S.count[buf][cell], kCap);
+    if (lane < n) {
+        const int gs = cell * kCap + lane;
+        txv[S.pid[buf][gs]] = S.tpv[buf][gs];
+    }
+}
+
+// Body tangent [B, 6] in (NULL: zero) / out.
+__global__ void body_tangent_kernel(SimDev S, const double* __restrict__ in, double* __restrict__ out)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= S.B) return;
+    BodyDev& b = S.body[t];
+    if (out) {
+        double* o = out + 6 * t;
+        o[0] = b.tr[0];
+        o[1] = b.tr[1];
+        o[2] = b.tth;
+        o[3] = b.tv[0];
+        o[4] = b.tv[1];
+        o[5] = b.tw;
+        return;
+    }
+    const double* s = in ? in + 6 * t : nullptr;
+    b.tr[0] = s ? s[0] : 0.0;
+    b.tr[1] = s ? s[1] : 0.0;
+    b.tth = s ? s[2] : 0.0;
+    b.tv[0] = s ? s[3] : 0.0;
+    b.tv[1] = s ? s[4] : 0.0;
+    b.tw = s ? s[5] : 0.0;
+    b.ftr[0] = (float)b.tr[0];
+    b.ftr[1] = (float)b.tr[1];
+    b.ftth = (float)b.tth;
+    b.ftv[0] = (float)b.tv[0];
+    b.ftv[1] = (float)b.tv[1];
+    b.ftw = (float)b.tw;
+}
+
 __global__ void set_run_kernel(RunDev* run, RunDev desc)
 {
     desc.step = run->step;
@@ -743,11 +952,19 @@ static cudaError_t launch(void (*k)(KArgs...), int grid, int block, cudaStream_t
 
 template <int TX, int TY>
 static cudaError_t launch_tile_phase(const SimDev& S, const EvalOut& E, int eval, int n_tiles, int phase,
-                                     cudaStream_t st, bool pdl)
+                                     cudaStream_t st, bool pdl, bool tan)
 {
     using Sh = Shape<TX, TY>;
-    if (phase == 0) return launch(density_kernel<TX, TY>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
-    return launch(force_kernel<TX, TY>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+    if (tan) {
+        if constexpr (TX * TY <= 32) {  // the tangent staging of 8x8 tiles exceeds static shared memory
+            if (phase == 0) return launch(density_kernel<TX, TY, true>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+            return launch(force_kernel<TX, TY, true>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (phase == 0) return launch(density_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+    return launch(force_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
 }
 
 void tile_dims(int code, int* tx, int* ty)
@@ -759,23 +976,23 @@ void tile_dims(int code, int* tx, int* ty)
 
 // phase 0: density pass, phase 1: force pass
 cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, int phase,
-                         cudaStream_t st, bool pdl)
+                         cudaStream_t st, bool pdl, bool tan)
 {
     switch (tile_code) {
-    case 1: return launch_tile_phase<2, 2>(S, E, eval, n_tiles, phase, st, pdl);
-    case 2: return launch_tile_phase<4, 2>(S, E, eval, n_tiles, phase, st, pdl);
-    case 3: return launch_tile_phase<4, 4>(S, E, eval, n_tiles, phase, st, pdl);
-    case 4: return launch_tile_phase<8, 4>(S, E, eval, n_tiles, phase, st, pdl);
-    case 5: return launch_tile_phase<8, 8>(S, E, eval, n_tiles, phase, st, pdl);
+    case 1: return launch_tile_phase<2, 2>(S, E, eval, n_tiles, phase, st, pdl, tan);
+    case 2: return launch_tile_phase<4, 2>(S, E, eval, n_tiles, phase, st, pdl, tan);
+    case 3: return launch_tile_phase<4, 4>(S, E, eval, n_tiles, phase, st, pdl, tan);
+    case 4: return launch_tile_phase<8, 4>(S, E, eval, n_tiles, phase, st, pdl, tan);
+    case 5: return launch_tile_phase<8, 8>(S, E, eval, n_tiles, phase, st, pdl, tan);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, cudaStream_t st,
-                        bool pdl)
+                        bool pdl, bool tan)
 {
     for (int ph = 0; ph < 2; ++ph) {
-        cudaError_t e = launch_phase(S, E, eval, tile_code, n_tiles, ph, st, pdl);
+        cudaError_t e = launch_phase(S, E, eval, tile_code, n_tiles, ph, st, pdl, tan);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -803,6 +1020,20 @@ cudaError_t launch_get_state(const SimDev& S, float* xv, double* body, int n_cel
 cudaError_t launch_set_run(RunDev* run, const RunDev& desc, cudaStream_t st)
 {
     set_run_kernel<<<1, 1, 0, st>>>(run, desc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tangent_state(const SimDev& S, const float* txv_in, float* txv_out, const double* tb_in,
+                                 double* tb_out, int n_cells_total, int buf, cudaStream_t st)
+{
+    const int grid = (n_cells_total + 7) / 8;
+    if (txv_out) {
+        if (n_cells_total > 0) gather_tangent_kernel<<<grid, 256, 0, st>>>(S, (float4*)txv_out, n_cells_total, buf);
+        if (tb_out) body_tangent_kernel<<<(S.B + 127) / 128, 128, 0, st>>>(S, nullptr, tb_out);
+    } else {
+        if (n_cells_total > 0) scatter_tangent_kernel<<<grid, 256, 0, st>>>(S, (const float4*)txv_in, n_cells_total, buf);
+        body_tangent_kernel<<<(S.B + 127) / 128, 128, 0, st>>>(S, tb_in, nullptr);
+    }
     return cudaGetLastError();
 }
 

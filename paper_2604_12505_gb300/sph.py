@@ -151,6 +151,24 @@ class Sim:
         check(lib().sph_relax(self._h, n_steps, damping, _stream(stream)), "sph_relax")
         self.steps_done += n_steps
 
+    def jvp(self, K: int, u=None, du=None, dxv0=None, dbody0=None, stream=None):
+        """Forward-mode derivative of K steps along the trajectory they compute.
+        Returns (y, dy, dxv, dbody): primal samples [B, n, 11], their tangent,
+        and the tangent of the final fluid [N, 4] and body [B, 6] state."""
+        u = None if u is None else _dev(u, torch.float64).reshape(self.B, K, 3)
+        du = None if du is None else _dev(du, torch.float64).reshape(self.B, K, 3)
+        dxv0 = None if dxv0 is None else _dev(dxv0, torch.float32).reshape(self.n_total, 4)
+        dbody0 = None if dbody0 is None else _dev(dbody0, torch.float64).reshape(self.B, 6)
+        ns = self.samples_for(K)
+        y = torch.zeros((self.B, ns, NY), dtype=torch.float64, device="cuda")
+        dy = torch.zeros_like(y)
+        dxv = torch.empty((self.n_total, 4), dtype=torch.float32, device="cuda")
+        dbody = torch.empty((self.B, 6), dtype=torch.float64, device="cuda")
+        check(lib().sph_jvp(self._h, _ptr(u), _ptr(du), _ptr(dxv0), _ptr(dbody0), K, _ptr(y), _ptr(dy), _ptr(dxv),
+                            _ptr(dbody), _stream(stream)), "sph_jvp")
+        self.steps_done += K
+        return y, dy, dxv, dbody
+
     def eval(self, u=None, stream=None):
         """Algorithm 1 on the current state without stepping."""
         N = self.n_total
