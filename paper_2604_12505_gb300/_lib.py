@@ -78,6 +78,17 @@ def _declare(L):
         "sph_time_kernels": ([vp, i32, dp, vp], C.c_int),
         "sph_run_batch": ([P, i32, vp, i32, C.POINTER(SphCtrl), vp, ip, vp], C.c_int),
         "sph_density_noalloc": ([P, vp, i32, vp, i32, dp, vp, vp], C.c_int),
+        "lpv_create": ([vp, C.POINTER(vp)], C.c_int),
+        "lpv_destroy": ([vp], C.c_int),
+        "lpv_set_params": ([vp, vp, vp], C.c_int),
+        "lpv_get_params": ([vp, vp, vp], C.c_int),
+        "lpv_normalize": ([vp, vp, vp, vp, i32, i32, vp], C.c_int),
+        "lpv_init_ls": ([vp, vp, vp, i32, i32, vp, vp], C.c_int),
+        "lpv_loss_grad": ([vp, vp, vp, vp, i32, i32, dp, vp, vp], C.c_int),
+        "lpv_train": ([vp, vp, vp, vp, i32, i32, i32, vp, vp], C.c_int),
+        "lpv_fit": ([vp, vp, vp, i32, i32, vp, C.POINTER(vp), dp, vp], C.c_int),
+        "lpv_predict": ([vp, vp, vp, i32, i32, vp, vp], C.c_int),
+        "lpv_simulate": ([vp, i32, vp, vp, vp, vp, i32, vp, vp, vp], C.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
