@@ -7,7 +7,11 @@ step.  One benchmark step = ``--inner`` inner SPH steps (default 1000)
 replayed from captured CUDA graphs; L2 is flushed between benchmark steps.
 
 Metric: pair interactions per second (ordered fluid pairs with r < 2h plus
-fluid-ghost pairs with r < h, counted exactly by the force kernel).
+fluid-ghost pairs with r < h, counted exactly by the force kernel).  After
+the timed region, the ``surrogate`` object reports the second half of the
+metric: closed-loop simulations per second of the LPV surrogate against the
+SPH simulator on 64 held-out manoeuvres, with the surrogate's NRMSE per body
+channel (data set of 256 batched tanks x 4 launches, dt = 2e-4 s).
 
 Arms:
   default            the CUDA library; prints one JSON line (rank 0).
@@ -46,6 +50,8 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--relax", type=int, default=40000, help="damped relaxation steps before timing")
+    ap.add_argument("--surrogate", default="full", choices=["full", "small", "off"],
+                    help="surrogate study after the timed region (rank 0): data set, fit, closed loop")
     return ap.parse_args()
 
 
@@ -181,6 +187,45 @@ def run_reference(a):
 
 
 # --------------------------------------------------------------------------
+SURROGATE_SIZES = {
+    # 256 tanks x 4 launches = 1024 trajectories of 1000 samples; 64 held-out
+    # closed-loop manoeuvres of 5000 steps; 65,536 surrogate runs
+    "full": dict(n_tanks=256, launches=4, steps=10_000, relax=5000, cl_tanks=64, cl_steps=5000, n_sims=65_536,
+                 fit_cfg=dict(adam_iters=2000, restarts=8)),
+    "small": dict(n_tanks=32, launches=1, steps=10_000, relax=5000, cl_tanks=16, cl_steps=5000, n_sims=65_536,
+                  fit_cfg=dict(adam_iters=300, restarts=2)),
+}
+
+
+def surrogate(size: str) -> dict:
+    """Surrogate-versus-simulator part of the metric: closed-loop simulations
+    per second of the LPV surrogate and of the SPH simulator on the same
+    held-out manoeuvres, with the surrogate's NRMSE against the simulator."""
+    from paper_2604_12505_gb300 import pipeline
+
+    kw = SURROGATE_SIZES[size]
+    t0 = time.perf_counter()
+    r = pipeline.surrogate_study(**kw)
+    cl, th, ds = r["closed_loop_lpv"], r["throughput"], r["dataset"]
+    short = lambda c: {"attitude": c["nrmse_attitude"], "translation": c["nrmse_translation"], "mean": c["nrmse_mean"]}
+    return {
+        "size": size,
+        "surrogate_sims_per_s": th["surrogate_sims_per_s"], "sph_sims_per_s": th["sph_sims_per_s"],
+        "speedup": th["speedup"],
+        "nrmse": cl["nrmse"], "nrmse_attitude": cl["nrmse_attitude"], "nrmse_translation": cl["nrmse_translation"],
+        "attitude_within_5pct": cl["nrmse_attitude"] <= 0.05, "all_channels_within_5pct": max(cl["nrmse"].values()) <= 0.05,
+        "baselines": {"lti": short(r["closed_loop_lti"]), "no_fluid": short(r["closed_loop_no_fluid"])},
+        "closed_loop": {"sims": th["surrogate_sims"], "sph_sims": th["sph_sims"], "steps": th["steps"],
+                        "periods": th["periods"], "dt": th["dt"], "Ts": th["Ts"], "surrogate_s": th["surrogate_s"],
+                        "sph_s": th["sph_s"]},
+        "dataset": {k: ds[k] for k in ("trajectories", "samples", "tanks", "particles", "batched_ms_per_step",
+                                       "sequential_ms_per_step", "batched_speedup", "sequential_sample")},
+        "fit": {"lpv": {k: r["fit_lpv"][k] for k in ("train_loss", "seconds")},
+                "lti": {k: r["fit_lti"][k] for k in ("train_loss", "seconds")}},
+        "wall_s": time.perf_counter() - t0,
+    }
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -303,10 +348,12 @@ def run_ours(a):
         "us_per_inner_step": 1e6 * T / (K * inner),
         "pairs_per_inner_step": pairs / (K * inner * world),
     }
+    sim.close()
+    if a.surrogate != "off":
+        out["surrogate"] = surrogate(a.surrogate)
     if not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, a.cpu_seconds)
     print(json.dumps(out), flush=True)
-    sim.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -37,6 +37,7 @@ typedef struct lpv_config {
     double sigma2;               /* l2 weight of the parameters, Eq. 27 (paper: 1e-4)   */
     double init_scale;           /* std of the normal draw of M_1..M_np per restart      */
     uint64_t seed;               /* seed of that draw                                    */
+    double rho_max;              /* spectral radius bound of the least-squares start     */
 } lpv_config;
 
 /* Rigid body and attitude controller of the closed loop (Eq. 20 without fluid
@@ -73,6 +74,17 @@ int lpv_get_params(const lpv_model* m, float* W, float* scales);
  *   y_k = sum_{i=1..na} A_i y_{k-i} + sum_{i=1..na} B_i u_{k-i}
  * on the normalised data (normal equations accumulated and solved in FP64 on
  * the device), written as M_0 in observer-canonical form; M_i (i >= 1) = 0.
+ * The start is a stable model: when the spectral radius rho of the state
+ * matrix exceeds cfg.rho_max (> 0), every characteristic root is scaled by
+ * lam = rho_max / rho (A_i <- lam^i A_i, B_i <- lam^i B_i, so the impulse
+ * response h_k becomes lam^k h_k); rho is estimated on the device from
+ * ||A^(2^s)||^(1/2^s) by 40 normalised FP64 squarings.  With 0 < rho_max < 1
+ * that stable model is then handed over as its balanced realisation (equal,
+ * diagonal controllability and observability Gramians, states by decreasing
+ * Hankel singular value, each column of C signed so that its largest entry is
+ * positive): the same input-output map, but without the near-defective
+ * companion structure whose poles move by O(delta^(1/n)) under rounding of
+ * the weights.
  * theta_out (host, may be NULL) receives the regression coefficients
  * [na*n_y + na*n_u][n_y] (rows: y_{k-1}..y_{k-na}, u_{k-1}..u_{k-na}).  Blocks.
  */
@@ -93,16 +105,23 @@ int lpv_loss_grad(lpv_model* m, const float* u, const float* y, const float* p, 
 
 /*
  * iters Adam steps on the data (Section 4: Adam before L-BFGS; L-BFGS is not
- * implemented).  loss_history (host [iters], may be NULL).  Blocks.
+ * implemented).  A step whose loss comes out non-finite or more than ten
+ * times the loss of the last accepted iterate is rejected: the weights return
+ * to that iterate and the same Adam direction is retried with half the step
+ * (the halving persists until the optimiser is reset by lpv_set_params or
+ * lpv_init_ls).  loss_history (host [iters], may be NULL) records the loss of
+ * every iterate tried.  Blocks.
  */
 int lpv_train(lpv_model* m, const float* u, const float* y, const float* p, int32_t n_traj, int32_t T,
               int32_t iters, double* loss_history, void* stream);
 
 /*
  * The identification of Section 5.3.2: lpv_normalize, lpv_init_ls, then for
- * each restart M_1..M_np drawn from N(0, init_scale^2) and adam_iters Adam
- * steps; keeps the restart with the lowest training loss.  best_loss (host)
- * may be NULL.  Blocks.
+ * each restart the B and C blocks of M_1..M_np drawn from N(0,
+ * init_scale^2) (their A blocks start at 0, so the start keeps the stable
+ * spectrum of M_0 for every p) and adam_iters Adam steps; keeps the restart with the lowest training loss.  best_loss (host)
+ * may be NULL.  Returns SPH_E_DIVERGED (and no model) when no restart ends
+ * with a finite loss.  Blocks.
  */
 int lpv_fit(const float* u, const float* y, const float* p, int32_t n_traj, int32_t T, const lpv_config* cfg,
             lpv_model** out, double* best_loss, void* stream);

@@ -128,6 +128,47 @@ def arx_to_ss(A, B):
     return As, Bs, Cs
 
 
+def stabilize(A, B, rho_max):
+    """Stable LTI start (the paper starts from a stable identified model): if
+    the spectral radius rho of the observer-canonical state matrix exceeds
+    rho_max, every characteristic root is scaled by lam = rho_max / rho via
+    A_i <- lam^i A_i, B_i <- lam^i B_i (impulse response h_k -> lam^k h_k).
+    Returns (A, B, rho)."""
+    As, _, _ = arx_to_ss(A, B)
+    rho = float(np.max(np.abs(np.linalg.eigvals(As)))) if As.size else 0.0
+    if rho_max <= 0 or rho <= rho_max:
+        return [a.copy() for a in A], [b.copy() for b in B], rho
+    lam = rho_max / rho
+    return ([lam ** (i + 1) * a for i, a in enumerate(A)], [lam ** (i + 1) * b for i, b in enumerate(B)], rho)
+
+
+def balance(As, Bs, Cs, reg=1e-12):
+    """Balanced realisation (Moore 1981) of a stable (A, B, C), the form in
+    which the least-squares start is handed to training: with the Gramians
+    P = A P A^T + B B^T and Q = A^T Q A + C^T C (each regularised by
+    reg * trace * I), P = Lp Lp^T, Q = Lq Lq^T and Lq^T Lp = U S V^T,
+    T = Lp V S^(-1/2) and T^-1 = S^(-1/2) U^T Lq^T give (T^-1 A T, T^-1 B, C T),
+    whose Gramians both equal diag(S).  States are ordered by decreasing S and
+    signed so that the largest-magnitude entry of each column of C T is
+    positive.  Returns (A, B, C, S)."""
+    import scipy.linalg as sl
+
+    n = As.shape[0]
+    P = sl.solve_discrete_lyapunov(As, Bs @ Bs.T)
+    Q = sl.solve_discrete_lyapunov(As.T, Cs.T @ Cs)
+    P = P + reg * np.trace(P) * np.eye(n)
+    Q = Q + reg * np.trace(Q) * np.eye(n)
+    Lp = np.linalg.cholesky(P)
+    Lq = np.linalg.cholesky(Q)
+    U, S, Vt = np.linalg.svd(Lq.T @ Lp)
+    T = Lp @ Vt.T / np.sqrt(S)
+    Ti = (U / np.sqrt(S)).T @ Lq.T
+    Ab, Bb, Cb = Ti @ As @ T, Ti @ Bs, Cs @ T
+    sign = np.sign(Cb[np.argmax(np.abs(Cb), axis=0), np.arange(n)])
+    sign[sign == 0] = 1.0
+    return sign[:, None] * Ab * sign[None, :], sign[:, None] * Bb, Cb * sign[None, :], S
+
+
 def ss_to_W(As, Bs, Cs, n_p):
     """W = [M_0, 0, ..., 0] with M_0 = [[A, B], [C, 0]]."""
     nx, nu = Bs.shape
@@ -137,6 +178,17 @@ def ss_to_W(As, Bs, Cs, n_p):
     M0[:nx, nx:] = Bs
     M0[nx:, :nx] = Cs
     return np.concatenate([M0] + [np.zeros_like(M0)] * n_p, axis=1)
+
+
+def ls_start(U, Y, na, rho_max, n_p):
+    """The least-squares start W = [M_0, 0, ..]: ARX fit, roots scaled into
+    |z| <= rho_max, observer-canonical form, balanced when 0 < rho_max < 1."""
+    A, B = arx_ls(U, Y, na, na)
+    A, B, _ = stabilize(A, B, rho_max)
+    As, Bs, Cs = arx_to_ss(A, B)
+    if 0.0 < rho_max < 1.0:
+        As, Bs, Cs, _ = balance(As, Bs, Cs)
+    return ss_to_W(As, Bs, Cs, n_p)
 
 
 # --------------------------------------------------------------------------

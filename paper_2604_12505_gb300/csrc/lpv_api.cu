@@ -28,8 +28,10 @@ struct lpv_model {
     size_t warp_cap = 0;
     double *d_loss = nullptr, *d_hist = nullptr;
     int hist_len = 0;
-    double *stats_part = nullptr, *stats = nullptr, *gram_part = nullptr, *theta = nullptr;
+    double *stats_part = nullptr, *stats = nullptr, *gram_part = nullptr, *theta = nullptr, *rho = nullptr;
     int* status = nullptr;
+    float *Wb = nullptr, *mb = nullptr, *vb = nullptr, *lr_scale = nullptr;  // last accepted Adam iterate
+    double* acc_loss = nullptr;                                              // and its loss
     int adam_t = 0;
 };
 
@@ -42,6 +44,20 @@ int err(int code, const std::string& msg) { return sph::set_last_error(code, msg
         cudaError_t e_ = (call);                                                                    \
         if (e_ != cudaSuccess) return err(SPH_E_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
     } while (0)
+
+// Adam restarts from the current weights: zero moments, the current weights as
+// the last accepted iterate, full step size.
+int reset_optimizer(lpv_model* M)
+{
+    for (float* p : {M->m, M->v, M->mb, M->vb}) LCK(cudaMemset(p, 0, kWN * sizeof(float)));
+    LCK(cudaMemcpy(M->Wb, M->Wp, kWN * sizeof(float), cudaMemcpyDeviceToDevice));
+    const float one = 1.f;
+    const double inf = INFINITY;
+    LCK(cudaMemcpy(M->lr_scale, &one, sizeof(float), cudaMemcpyHostToDevice));
+    LCK(cudaMemcpy(M->acc_loss, &inf, sizeof(double), cudaMemcpyHostToDevice));
+    M->adam_t = 0;
+    return SPH_OK;
+}
 
 template <class T>
 int grow(T** p, size_t* cap, size_t n)
@@ -116,10 +132,14 @@ int lpv_create(const lpv_config* cfg, lpv_model** out)
               cudaMalloc(&M->stats, 32 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&M->gram_part, (size_t)gram_blocks() * 1024 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&M->theta, 32 * 16 * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&M->status, sizeof(int)) == cudaSuccess;
-    if (ok) ok = cudaMemset(M->Wp, 0, kWN * sizeof(float)) == cudaSuccess &&
-                 cudaMemset(M->m, 0, kWN * sizeof(float)) == cudaSuccess &&
-                 cudaMemset(M->v, 0, kWN * sizeof(float)) == cudaSuccess;
+              cudaMalloc(&M->rho, sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&M->status, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&M->Wb, kWN * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&M->mb, kWN * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&M->vb, kWN * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&M->lr_scale, sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&M->acc_loss, sizeof(double)) == cudaSuccess;
+    if (ok) ok = cudaMemset(M->Wp, 0, kWN * sizeof(float)) == cudaSuccess && reset_optimizer(M) == SPH_OK;
     if (!ok) {
         lpv_destroy(M);
         return err(SPH_E_NOMEM, "lpv_create: allocation failed");
@@ -134,7 +154,8 @@ int lpv_destroy(lpv_model* M)
     cudaDeviceSynchronize();
     for (void* p : {(void*)M->Wp, (void*)M->m, (void*)M->v, (void*)M->grad, (void*)M->hist, (void*)M->gpart,
                     (void*)M->loss_part, (void*)M->d_loss, (void*)M->d_hist, (void*)M->stats_part, (void*)M->stats,
-                    (void*)M->gram_part, (void*)M->theta, (void*)M->status})
+                    (void*)M->gram_part, (void*)M->theta, (void*)M->rho, (void*)M->status, (void*)M->Wb,
+                    (void*)M->mb, (void*)M->vb, (void*)M->lr_scale, (void*)M->acc_loss})
         cudaFree(p);
     delete M;
     return SPH_OK;
@@ -152,9 +173,7 @@ int lpv_set_params(lpv_model* M, const float* W, const float* scales)
                 for (int f = 0; f < nc; ++f)
                     if (trainable(d, o, kt * kFB + f)) Wp[o * kFB * kMaxKT + kt * kFB + f] = W[(kt * nr + o) * nc + f];
         LCK(cudaMemcpy(M->Wp, Wp.data(), kWN * sizeof(float), cudaMemcpyHostToDevice));
-        LCK(cudaMemset(M->m, 0, kWN * sizeof(float)));
-        LCK(cudaMemset(M->v, 0, kWN * sizeof(float)));
-        M->adam_t = 0;
+        if (int rc = reset_optimizer(M)) return rc;
     }
     if (scales) {
         Dims& dm = M->d;
@@ -230,16 +249,14 @@ int lpv_init_ls(lpv_model* M, const float* u, const float* y, int32_t n_traj, in
     cudaStream_t st = (cudaStream_t)stream;
     const int na = M->cfg.na;
     LCK(launch_gram(u, y, n_traj, T, M->d, na, M->gram_part, st));
-    LCK(launch_ls_solve(M->gram_part, M->d, na, M->theta, M->Wp, M->status, st));
+    LCK(launch_ls_solve(M->gram_part, M->d, na, M->cfg.rho_max, M->theta, M->Wp, M->status, M->rho, st));
     int status = 0;
     LCK(cudaMemcpyAsync(&status, M->status, sizeof(int), cudaMemcpyDeviceToHost, st));
     LCK(cudaStreamSynchronize(st));
     if (status) return err(SPH_E_DIVERGED, "lpv_init_ls: the normal equations are not positive definite");
     const int nreg = na * (M->d.ny + M->d.nu);
     if (theta_out) LCK(cudaMemcpy(theta_out, M->theta, (size_t)nreg * M->d.ny * sizeof(double), cudaMemcpyDeviceToHost));
-    LCK(cudaMemset(M->m, 0, kWN * sizeof(float)));
-    LCK(cudaMemset(M->v, 0, kWN * sizeof(float)));
-    M->adam_t = 0;
+    return reset_optimizer(M);
     return SPH_OK;
 }
 
@@ -302,7 +319,7 @@ int lpv_train(lpv_model* M, const float* u, const float* y, const float* p, int3
         if (rc) return rc;
         const int t = ++M->adam_t;
         const float c1 = (float)(1.0 / (1.0 - std::pow(c.beta1, t))), c2 = (float)(1.0 / (1.0 - std::pow(c.beta2, t)));
-        LCK(launch_adam(M->Wp, M->m, M->v, M->grad, M->d, (float)c.lr, (float)c.beta1, (float)c.beta2,
+        LCK(launch_adam(M->Wp, M->m, M->v, M->Wb, M->mb, M->vb, M->lr_scale, M->acc_loss, M->grad, M->d_loss, M->d, (float)c.lr, (float)c.beta1, (float)c.beta2,
                         (float)c.adam_eps, c1, c2, st));
     }
     LCK(cudaStreamSynchronize(st));
@@ -331,11 +348,17 @@ int lpv_fit(const float* u, const float* y, const float* p, int32_t n_traj, int3
     double best = INFINITY;
     const int restarts = cfg->restarts > 0 ? cfg->restarts : 1;
     for (int r = 0; r < restarts; ++r) {
-        // M_0 from the least-squares fit, M_i ~ N(0, init_scale^2) (Section 5.3.2)
+        // M_0 from the least-squares fit; the B and C blocks of M_i ~ N(0,
+        // init_scale^2) (Section 5.3.2), their A blocks 0 so that A(p) = A_0
+        // keeps the stable spectrum of the start for every p
         std::mt19937_64 gen(cfg->seed + 1000003ull * (uint64_t)r);
         std::normal_distribution<double> nd(0.0, cfg->init_scale);
         W = W0;
-        for (int i = nr * nc; i < nw; ++i) W[i] = (float)nd(gen);
+        for (int i = nr * nc; i < nw; ++i) {
+            const int o = (i / nc) % nr, f = i % nc;
+            const double draw = nd(gen);
+            W[i] = (o < d.nx && f < d.nx) ? 0.f : (float)draw;
+        }
         if ((rc = lpv_set_params(M, W.data(), nullptr))) return bail(rc);
         if ((rc = lpv_train(M, u, y, p, n_traj, T, cfg->adam_iters, nullptr, stream))) return bail(rc);
         double L = 0.0;
@@ -344,6 +367,10 @@ int lpv_fit(const float* u, const float* y, const float* p, int32_t n_traj, int3
             best = L;
             if ((rc = lpv_get_params(M, Wbest.data(), nullptr))) return bail(rc);
         }
+    }
+    if (!std::isfinite(best)) {
+        lpv_destroy(M);
+        return err(SPH_E_DIVERGED, "lpv_fit: no restart ended with a finite training loss");
     }
     if ((rc = lpv_set_params(M, Wbest.data(), nullptr))) return bail(rc);
     if (best_loss) *best_loss = best;

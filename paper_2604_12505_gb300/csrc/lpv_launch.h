@@ -28,8 +28,9 @@ cudaError_t launch_closed_loop(const float* Wp, const Dims& d, int B, int T, con
 cudaError_t launch_reduce(const float* gpart, int n_warps, const double* loss_part, const float* Wp, const Dims& d,
                           double sigma2, double n_samples, float* grad, double* loss, double* loss_hist, int it,
                           cudaStream_t st);
-cudaError_t launch_adam(float* Wp, float* m, float* v, const float* grad, const Dims& d, float lr, float b1, float b2,
-                        float eps, float c1, float c2, cudaStream_t st);
+cudaError_t launch_adam(float* Wp, float* m, float* v, float* Wb, float* mb, float* vb, float* lr_scale,
+                        double* acc_loss, const float* grad, const double* loss, const Dims& d, float lr, float b1,
+                        float b2, float eps, float c1, float c2, cudaStream_t st);
 // Per channel over n rows: sum u^2 (n_u), sum y^2 (n_y), sum p and sum p^2 (n_p),
 // written to stats[n_u + n_y + 2 n_p] (FP64).  part: scratch of 256 x 32 doubles.
 cudaError_t launch_stats(const float* u, const float* y, const float* p, long long n, int nu, int ny, int np,
@@ -41,7 +42,9 @@ cudaError_t launch_stats(const float* u, const float* y, const float* p, long lo
 int gram_blocks();
 cudaError_t launch_gram(const float* u, const float* y, int n_traj, int T, const Dims& d, int na, double* part,
                         cudaStream_t st);
-cudaError_t launch_ls_solve(const double* part, const Dims& d, int na, double* theta, float* Wp, int* status,
-                            cudaStream_t st);
+// rho_max > 0: the roots of the start are scaled into |z| <= rho_max; rho_out
+// (device, may be NULL) receives the spectral radius before scaling.
+cudaError_t launch_ls_solve(const double* part, const Dims& d, int na, double rho_max, double* theta, float* Wp,
+                            int* status, double* rho_out, cudaStream_t st);
 
 }  // namespace lpv

@@ -12,11 +12,13 @@ from .sph import _dev, _ptr, _stream
 
 
 class LpvConfig(C.Structure):
+    """Mirror of ``lpv_config`` (96 bytes, field order matters)."""
+
     _fields_ = [
         ("n_x", C.c_int32), ("n_u", C.c_int32), ("n_y", C.c_int32), ("n_p", C.c_int32), ("na", C.c_int32),
         ("adam_iters", C.c_int32), ("restarts", C.c_int32), ("reserved", C.c_int32),
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("adam_eps", C.c_double),
-        ("sigma2", C.c_double), ("init_scale", C.c_double), ("seed", C.c_uint64),
+        ("sigma2", C.c_double), ("init_scale", C.c_double), ("seed", C.c_uint64), ("rho_max", C.c_double),
     ]
 
 
@@ -28,7 +30,7 @@ class LpvBody(C.Structure):
 
 
 DEFAULT = dict(n_x=12, n_u=3, n_y=4, n_p=2, na=3, adam_iters=2000, restarts=8, lr=1e-3, beta1=0.9, beta2=0.999,
-               adam_eps=1e-8, sigma2=1e-4, init_scale=1e-2, seed=7)
+               adam_eps=1e-8, sigma2=1e-4, init_scale=1e-2, seed=7, rho_max=0.999)
 
 
 def _vp(struct):

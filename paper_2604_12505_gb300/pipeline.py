@@ -1,0 +1,247 @@
+"""Data set generation with the batched simulator and surrogate evaluation.
+
+Tanks           a batch of independent tanks relaxed once (Section 5.1: the
+                fluid is spawned, then evolved without actuation until it is
+                at rest); its rest state is kept so that several manoeuvres
+                start from it.  ``run`` applies inputs held over each sampling
+                period (open loop, or under the PD attitude law of Eq. 28).
+dataset         the data set D_N of Eq. 2 from several launches of a batch.
+sequential_rate the same tanks stepped one at a time through the single-tank
+                path, for the batched-versus-sequential comparison.
+nrmse           1 - BFR / 100 per channel (BFR: footnote in Section 5.3.2).
+
+Surrogate channels: input u = [F_x, F_y, tau] applied to the body; output
+y = [F_x, F_y, T] (the fluid loads on the body, Eq. 20) and the distance of
+the fluid centre of mass from the tank centre minus its value at rest;
+scheduling p = [fill fraction, body angular rate].
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+import torch
+
+from .sph import Sim
+
+
+class Tanks:
+    """B tanks (list of parameter dicts with one dt and outer_every) relaxed
+    with ``relax_steps`` damped steps; velocities are zeroed afterwards."""
+
+    def __init__(self, params: list[dict], relax_steps: int, damping: float = 4e-3, autotune: bool = True):
+        self.params = params
+        self.outer = params[0]["outer_every"]
+        self.sim = Sim(params)
+        if autotune:
+            self.sim.autotune(steps=10)
+        if relax_steps > 0:
+            self.sim.relax(relax_steps, damping=damping)
+        xv, body = self.sim.state()
+        xv[:, 2:] = 0.0
+        self.rest = (xv.clone(), body.clone())
+        self.sim.set_state(*self.rest)
+        self.sim.check()
+        self.fill = np.array([p["fill"] for p in params])
+        self.n_fluid = list(self.sim.n_fluid)
+
+    def run(self, u_samples: np.ndarray, ctrl: dict | None = None, theta_ref: np.ndarray | None = None):
+        """u_samples [B, K, 3] per sampling period, from the rest state.
+        Returns (samples [B, K, 11] float64 numpy, device seconds)."""
+        B, K, _ = u_samples.shape
+        self.sim.set_state(*self.rest)
+        u_inner = torch.tensor(np.repeat(u_samples, self.outer, axis=1), dtype=torch.float64, device="cuda")
+        ref = None if theta_ref is None else torch.tensor(theta_ref, dtype=torch.float64, device="cuda")
+        y = torch.zeros((B, K, 11), dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        self.sim.step(K * self.outer, u=u_inner, ctrl=ctrl, theta_ref=ref, y_out=y)
+        e1.record()
+        torch.cuda.synchronize()
+        self.sim.check()
+        return y.cpu().numpy(), e0.elapsed_time(e1) * 1e-3
+
+    def rest_of(self, b: int):
+        """Rest state (xv, body) of tank b alone."""
+        o = int(np.sum(self.n_fluid[:b]))
+        return self.rest[0][o:o + self.n_fluid[b]].clone(), self.rest[1][b:b + 1].clone()
+
+    def close(self):
+        self.sim.close()
+
+
+def surrogate_channels(y_raw: np.ndarray, fill: np.ndarray):
+    """(y [B, K, 4], p [B, K, 2]) from the simulator samples [B, K, 11]."""
+    off = np.linalg.norm(y_raw[:, :, 9:11] - y_raw[:, :, 0:2], axis=2)
+    y = np.concatenate([y_raw[:, :, 6:9], (off - off[:, :1])[:, :, None]], axis=2)
+    p = np.stack([np.broadcast_to(fill[:, None], off.shape), y_raw[:, :, 5]], axis=2)
+    return y, p
+
+
+def dataset(tanks: Tanks, u_launches: list[np.ndarray]):
+    """D_N from one launch of the batch per input array [B, K, 3]: returns
+    dict(u, y, p [L*B, K, .], tank [L*B], seconds, steps) with trajectories
+    ordered launch-major."""
+    us, ys, ps, secs = [], [], [], 0.0
+    for u in u_launches:
+        y_raw, s = tanks.run(u)
+        y, p = surrogate_channels(y_raw, tanks.fill)
+        us.append(u)
+        ys.append(y)
+        ps.append(p)
+        secs += s
+    B = len(tanks.params)
+    K = u_launches[0].shape[1]
+    return dict(u=np.concatenate(us), y=np.concatenate(ys), p=np.concatenate(ps),
+                tank=np.tile(np.arange(B), len(u_launches)), seconds=secs, steps=len(u_launches) * K * tanks.outer)
+
+
+def sequential_rate(tanks: Tanks, which: list[int], n_steps: int):
+    """Device seconds per step of each listed tank run alone through the
+    single-tank path (same tile autotuning, same rest state)."""
+    out = []
+    for b in which:
+        s = Sim(tanks.params[b])
+        s.autotune(steps=10)
+        s.set_state(*tanks.rest_of(b))
+        s.step(32, record=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        s.step(n_steps, record=False)
+        e1.record()
+        torch.cuda.synchronize()
+        s.check()
+        out.append(e0.elapsed_time(e1) * 1e-3 / n_steps)
+        s.close()
+    return out
+
+
+def nrmse(y: np.ndarray, yh: np.ndarray) -> np.ndarray:
+    """1 - BFR / 100 per channel, BFR = 1 - ||y - yh|| / ||y - mean(y)||."""
+    num = np.sqrt(np.sum((y - yh) ** 2, axis=0))
+    den = np.sqrt(np.sum((y - y.mean(axis=0)) ** 2, axis=0))
+    return num / np.maximum(den, 1e-300)
+
+
+def _closed_loop_inputs(B: int, K: int, Ts: float, seed0: int):
+    """Held-out manoeuvres: F and tau from the data-set distribution, theta_ref random steps."""
+    from . import workloads as W
+
+    F = np.stack([W.piecewise_profile(K, Ts, seed=seed0 + b)[:, :2] for b in range(B)])
+    tau = np.stack([W.piecewise_profile(K, Ts, seed=seed0 + 10_000 + b)[:, 2] for b in range(B)])
+    ref = np.stack([W.theta_ref_steps(K, Ts, seed=seed0 + 20_000 + b) for b in range(B)])
+    return F, tau, ref
+
+
+def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, relax: int = 5000,
+                    dt: float = 2e-4, cl_tanks: int = 64, cl_steps: int = 5000, n_sims: int = 65_536,
+                    fit_cfg: dict | None = None, seq_tanks: int = 8, seq_steps: int = 1000, ctrl=None,
+                    log=None) -> dict:
+    """The surrogate workflow on the simulator and the LPV library.
+
+    1. D_N: n_tanks tanks (fill, dx from the data-set distribution) relaxed
+       once, ``launches`` open-loop runs of ``steps`` steps each with seeded
+       piecewise-constant inputs; the batch step rate against the same tanks
+       stepped one at a time.
+    2. Fit (lpv.fit) on the trajectories of the first 80 % of the tanks, for
+       the LPV model (p = [fill, thetadot]) and the LTI model (no scheduling).
+    3. cl_tanks unseen tanks under unseen manoeuvres in closed loop with the PD
+       attitude law (Eq. 28) for cl_steps steps, by the simulator and by the
+       surrogate; NRMSE per body channel, and throughput of n_sims surrogate
+       closed-loop runs against the simulator's.
+    """
+    from . import lpv
+    from . import workloads as W
+
+    say = log or (lambda *a: None)
+    ctrl = ctrl or dict(omega=0.2 * np.pi, xi=0.7)
+    out: dict = {}
+    params = [dict(p, dt=dt) for p in W.batch_tank_params(n_tanks, seed0=1000)]
+    outer = params[0]["outer_every"]
+    Ts = dt * outer
+    K = steps // outer
+    t0 = time.perf_counter()
+    tanks = Tanks(params, relax)
+    out["relax_wall_s"] = time.perf_counter() - t0
+    u_l = [np.stack([W.piecewise_profile(K, Ts, seed=100_000 + 1000 * l + b) for b in range(n_tanks)])
+           for l in range(launches)]
+    d = dataset(tanks, u_l)
+    npart = np.array(tanks.n_fluid, dtype=np.float64)
+    seq = sequential_rate(tanks, list(range(min(seq_tanks, n_tanks))), seq_steps)
+    s_batch = d["seconds"] / d["steps"]
+    s_seq = float(np.sum(seq) / npart[:len(seq)].sum() * npart.sum())
+    out["dataset"] = dict(trajectories=int(d["u"].shape[0]), samples=K, tanks=n_tanks, particles=int(npart.sum()),
+                          device_s=d["seconds"], batched_ms_per_step=1e3 * s_batch,
+                          sequential_ms_per_step=1e3 * s_seq, batched_speedup=s_seq / s_batch,
+                          sequential_sample=f"{len(seq)} of {n_tanks} tanks alone, {seq_steps} steps each, "
+                                            "scaled to all tanks by particle count")
+    say("dataset", out["dataset"])
+    tanks.close()
+
+    ntr = int(round(0.8 * n_tanks))
+    tr = d["tank"] < ntr
+    cfg = dict(lpv.DEFAULT, **(fit_cfg or {}))
+    u, y, p = d["u"], d["y"], d["p"]
+    fits = {}
+    for name, n_p in (("lpv", 2), ("lti", 0)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        model, best = lpv.fit(u[tr], y[tr], p[tr][:, :, :n_p], dict(cfg, n_p=n_p))
+        torch.cuda.synchronize()
+        fit_s = time.perf_counter() - t0
+        yh = model.predict(u[~tr], p[~tr][:, :, :n_p]).cpu().numpy()
+        e = np.mean([nrmse(a, b) for a, b in zip(y[~tr], yh)], axis=0)
+        fits[name] = model
+        out[f"fit_{name}"] = dict(train_loss=best, seconds=fit_s, test_nrmse_outputs=e.tolist())
+        say("fit", name, out[f"fit_{name}"])
+
+    pt = [dict(q, dt=dt) for q in W.batch_tank_params(cl_tanks, seed0=2000)]
+    Kc = cl_steps // outer
+    F, tau, ref = _closed_loop_inputs(cl_tanks, Kc, Ts, seed0=200_000)
+    tt = Tanks(pt, relax)
+    ys, sph_s = tt.run(np.concatenate([F, tau[:, :, None]], axis=2), ctrl=ctrl, theta_ref=ref)
+    ys = ys[:, :, :6]
+    fill = tt.fill
+    tt.close()
+    body = dict(m=pt[0]["m_body"], J=pt[0]["J_body"], Ts=Ts, n_sub=outer, ctrl_omega=ctrl["omega"],
+                ctrl_xi=ctrl["xi"])
+    names = ["r_x", "r_y", "theta", "rdot_x", "rdot_y", "thetadot"]
+
+    def cl_err(model):
+        yl = model.simulate(F, tau, ref, fill, body).cpu().numpy()
+        e = np.mean([nrmse(ys[b], yl[b]) for b in range(cl_tanks)], axis=0)
+        return dict(zip(names, e.tolist())), float(np.mean(e[[2, 5]])), float(np.mean(e[[0, 1, 3, 4]]))
+
+    none = lpv.Model(dict(fits["lpv"].cfg))
+    none.set_params(np.zeros(none.shape_W, dtype=np.float32), fits["lpv"].get_params()[1])
+    lti = lpv.Model(dict(fits["lpv"].cfg))
+    Wl = np.zeros(lti.shape_W, dtype=np.float32)
+    W0, s0 = fits["lti"].get_params()
+    Wl[0] = W0[0]
+    lti.set_params(Wl, np.concatenate([s0, fits["lpv"].get_params()[1][len(s0):]]))
+    for name, m in (("lpv", fits["lpv"]), ("lti", lti), ("no_fluid", none)):
+        per, att, trn = cl_err(m)
+        out[f"closed_loop_{name}"] = dict(nrmse=per, nrmse_attitude=att, nrmse_translation=trn,
+                                          nrmse_mean=float(np.mean(list(per.values()))))
+        say("closed loop", name, out[f"closed_loop_{name}"])
+
+    # throughput: n_sims surrogate runs (the held-out manoeuvres tiled), inputs resident
+    idx = np.arange(n_sims) % cl_tanks
+    dev = lambda a: torch.tensor(a[idx], dtype=torch.float64, device="cuda")
+    Fd, td, rd, fd = dev(F), dev(tau), dev(ref), dev(fill)
+    model = fits["lpv"]
+    model.simulate(Fd[:256], td[:256], rd[:256], fd[:256], body)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    model.simulate(Fd, td, rd, fd, body)
+    e1.record()
+    torch.cuda.synchronize()
+    lpv_s = e0.elapsed_time(e1) * 1e-3
+    out["throughput"] = dict(surrogate_sims=n_sims, surrogate_s=lpv_s, surrogate_sims_per_s=n_sims / lpv_s,
+                             sph_sims=cl_tanks, sph_s=sph_s, sph_sims_per_s=cl_tanks / sph_s,
+                             speedup=(n_sims / lpv_s) / (cl_tanks / sph_s), steps=cl_steps, periods=Kc, Ts=Ts, dt=dt)
+    say("throughput", out["throughput"])
+    return out

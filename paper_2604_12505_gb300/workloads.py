@@ -21,7 +21,7 @@ BASE = dict(
     k=3.0,
     alpha=8.32e-4,
     beta=4e-4,
-    gamma1=1.0,               # tuned against tunnelling with three ghost rings (Section 3.5)
+    gamma1=1.5,               # tuned against tunnelling with three ghost rings (Section 3.5)
     eps=0.01,
     m_body=500.0,
     J_body=50.0,
@@ -98,3 +98,16 @@ def unit_directions(n_dir: int, dim: int, seed: int) -> np.ndarray:
     """[n_dir, dim] directions ~ N(0, I), each normalised to unit length."""
     d = np.random.default_rng(seed).normal(size=(n_dir, dim))
     return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def theta_ref_steps(n_samples: int, Ts: float, seed: int, amp: float = 0.3, hold=(1.0, 3.0)) -> np.ndarray:
+    """[n_samples] attitude reference of random steps: values U[-amp, amp] rad
+    held for durations U[hold] seconds."""
+    rng = np.random.default_rng(seed)
+    out = np.zeros(n_samples)
+    k = 0
+    while k < n_samples:
+        n = max(1, int(round(rng.uniform(*hold) / Ts)))
+        out[k:k + n] = rng.uniform(-amp, amp)
+        k += n
+    return out

@@ -67,6 +67,73 @@ def test_observer_canonical_form_reproduces_the_arx_recursion():
     np.testing.assert_allclose(y_ss, _arx_sim(A, B, u), rtol=1e-12, atol=1e-12)
 
 
+def test_stabilize_scales_known_roots():
+    # scalar ARX(2) with roots 1.1 and 0.5: a1 = r1 + r2, a2 = -r1 r2
+    r1, r2, rho_max = 1.1, 0.5, 0.99
+    A = [np.array([[r1 + r2]]), np.array([[-r1 * r2]])]
+    B = [np.array([[1.0]]), np.array([[0.3]])]
+    As, Bs, rho = L.stabilize(A, B, rho_max)
+    lam = rho_max / r1
+    assert rho == pytest.approx(r1, rel=1e-13)
+    assert As[0][0, 0] == pytest.approx(lam * (r1 + r2), rel=1e-13)
+    assert As[1][0, 0] == pytest.approx(-lam * lam * r1 * r2, rel=1e-13)
+    assert Bs[0][0, 0] == pytest.approx(lam, rel=1e-13)
+    assert Bs[1][0, 0] == pytest.approx(0.3 * lam * lam, rel=1e-13)
+    # a stable model is left alone
+    A2, B2, rho2 = L.stabilize([np.array([[0.5]])], [np.array([[2.0]])], rho_max)
+    assert rho2 == pytest.approx(0.5) and A2[0][0, 0] == 0.5 and B2[0][0, 0] == 2.0
+
+
+def test_stabilize_discounts_the_impulse_response():
+    rng = np.random.default_rng(3)
+    A = [0.9 * rng.normal(size=(2, 2)) for _ in range(3)]
+    B = [rng.normal(size=(2, 1)) for _ in range(3)]
+    As, Bs, rho = L.stabilize(A, B, 0.95)
+    assert rho > 0.95
+    lam = 0.95 / rho
+    T = 40
+    u = np.zeros((T, 1))
+    u[0] = 1.0
+    h, hs = _arx_sim(A, B, u), _arx_sim(As, Bs, u)
+    np.testing.assert_allclose(hs, h * lam ** np.arange(T)[:, None], rtol=1e-10, atol=1e-12 * np.abs(h).max())
+
+
+def test_balance_first_order_closed_form():
+    # P = b^2 / (1 - a^2), Q = c^2 / (1 - a^2): S = |b c| / (1 - a^2), |b'| = |c'| = sqrt(|b c|)
+    a, b, c = 0.9, 3.0, -0.5
+    Ab, Bb, Cb, S = L.balance(np.array([[a]]), np.array([[b]]), np.array([[c]]), reg=0.0)
+    assert S[0] == pytest.approx(abs(b * c) / (1 - a * a), rel=1e-12)
+    assert Ab[0, 0] == pytest.approx(a, rel=1e-14)
+    assert Cb[0, 0] == pytest.approx(np.sqrt(abs(b * c)), rel=1e-12)
+    assert Bb[0, 0] == pytest.approx(np.sign(b * c) * np.sqrt(abs(b * c)), rel=1e-12)
+
+
+def test_balance_gramians_by_direct_sums_and_markov_parameters():
+    rng = np.random.default_rng(4)
+    A, B = _true_arx(rng, 2, 2, 3)
+    As, Bs, Cs = L.arx_to_ss(A, B)
+    assert np.abs(np.linalg.eigvals(As)).max() < 0.8
+    Ab, Bb, Cb, S = L.balance(As, Bs, Cs, reg=0.0)
+    # Gramians as the series sum_k A^k B B^T A^kT (and the dual), truncated where it has converged
+    P = np.zeros_like(Ab)
+    Q = np.zeros_like(Ab)
+    Ak = np.eye(len(Ab))
+    for _ in range(400):
+        P += Ak @ Bb @ Bb.T @ Ak.T
+        Q += Ak.T @ Cb.T @ Cb @ Ak
+        Ak = Ak @ Ab
+    np.testing.assert_allclose(P, np.diag(S), atol=1e-9 * S.max())
+    np.testing.assert_allclose(Q, np.diag(S), atol=1e-9 * S.max())
+    assert np.all(np.diff(S) <= 0)
+    M1, M2 = Cs @ Bs, Cb @ Bb
+    A1, A2 = np.eye(len(As)), np.eye(len(Ab))
+    for _ in range(30):
+        np.testing.assert_allclose(M2, M1, atol=1e-10 * np.abs(Cs @ Bs).max())
+        A1, A2 = A1 @ As, A2 @ Ab
+        M1, M2 = Cs @ A1 @ Bs, Cb @ A2 @ Bb
+    assert np.all(Cb[np.argmax(np.abs(Cb), axis=0), np.arange(len(Ab))] > 0)
+
+
 def test_bptt_gradient_matches_finite_differences():
     rng = np.random.default_rng(3)
     nx, nu, ny, n_p = 3, 2, 2, 2
