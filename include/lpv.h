@@ -58,7 +58,9 @@ int lpv_destroy(lpv_model* m);
 /*
  * Parameters in host memory.  W: float32 [1 + n_p][n_x + n_y][n_x + n_u], the
  * blocks M_0..M_np (entries of the D blocks are ignored and kept zero).
- * scales: float32 [n_u + n_y + 2 n_p] = s_u, s_y, m_p, s_p.
+ * scales: float32 [n_u + n_y + 4 n_p] = s_u, s_y, m_p, s_p, p_lo, p_hi: input
+ * and output scales, scheduling mean and standard deviation, and the range of
+ * the scheduling the model was identified on (+-inf: unbounded).
  */
 int lpv_set_params(lpv_model* m, const float* W, const float* scales);
 int lpv_get_params(const lpv_model* m, float* W, float* scales);
@@ -67,8 +69,9 @@ int lpv_get_params(const lpv_model* m, float* W, float* scales);
  * Data sets D_N (Eq. 2): u float32 [n_traj, T, n_u], y float32 [n_traj, T,
  * n_y], p float32 [n_traj, T, n_p], device.
  *
- * lpv_normalize: sets s_u, s_y to the root mean square and m_p, s_p to the
- * mean and standard deviation of each channel over the data (FP64 sums).
+ * lpv_normalize: sets s_u, s_y to the root mean square, m_p, s_p to the
+ * mean and standard deviation and p_lo, p_hi to the minimum and maximum of
+ * each channel over the data (FP64 sums).
  *
  * lpv_init_ls: FP64 least-squares fit of the MIMO ARX model
  *   y_k = sum_{i=1..na} A_i y_{k-i} + sum_{i=1..na} B_i u_{k-i}
@@ -134,7 +137,8 @@ int lpv_predict(const lpv_model* m, const float* u, const float* p, int32_t n_tr
  * Closed-loop batched simulation (Sections 5.1.1 and 5.4) of B independent
  * runs of T sampling periods: per period the PD torque of Eq. 28 is computed
  * from the sampled attitude and held, u = [F_x, F_y, tau + tau_c], p = [fill,
- * thetadot], the surrogate gives the sloshing loads (its first three outputs:
+ * thetadot] clamped to [p_lo, p_hi] (the model holds only on the scheduling
+ * range it was identified on), the surrogate gives the sloshing loads (its first three outputs:
  * F_x, F_y, T on the body), and the rigid body (Eq. 20) takes n_sub
  * kick-then-drift substeps under them.  Inputs (device, float64): F [B, T, 2],
  * tau [B, T], theta_ref [B, T], fill [B].  Output out float64 [B, T, 6]:

@@ -206,7 +206,7 @@ def adam_step(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 # --------------------------------------------------------------------------
 # closed loop: rigid body + surrogate sloshing loads + PD attitude control
 # --------------------------------------------------------------------------
-def closed_loop(W, nx, scales, body, fill, F, tau, theta_ref, Ts, n_sub, pd):
+def closed_loop(W, nx, scales, body, fill, F, tau, theta_ref, Ts, n_sub, pd, p_range=None):
     """One closed-loop run at the sampling period Ts (Section 5.1.1):
       tau_c,k = J w^2 (theta_ref_k - theta_k) - 2 xi J w thetadot_k   (Eq. 28, ZOH)
       u_k = [F_x, F_y, tau + tau_c],  p_k = [fill, thetadot_k]
@@ -214,8 +214,10 @@ def closed_loop(W, nx, scales, body, fill, F, tau, theta_ref, Ts, n_sub, pd):
       sloshing loads [F_bx, F_by, T_b] = y_k[:3] * y_scale[:3]
       body (Eq. 20 with the loads held over the period): n_sub kick-then-drift
       substeps of Ts / n_sub.
-    scales: dict(u, y, p_mean, p_scale).  Returns [T, 6] samples (before each
-    period) of r_x, r_y, theta, rdot_x, rdot_y, thetadot."""
+    scales: dict(u, y, p_mean, p_scale).  p_range (lo, hi), if given: p is
+    clamped to it (the range the model was identified on) before scaling.
+    Returns [T, 6] samples (before each period) of r_x, r_y, theta, rdot_x,
+    rdot_y, thetadot."""
     m, J = body["m"], body["J"]
     Jc = pd.get("J", J) if pd.get("J", 0) > 0 else J
     w, xi = pd["omega"], pd["xi"]
@@ -228,7 +230,10 @@ def closed_loop(W, nx, scales, body, fill, F, tau, theta_ref, Ts, n_sub, pd):
         out[k] = s
         tc = Jc * w * w * (theta_ref[k] - s[2]) - 2.0 * xi * Jc * w * s[5]
         u = np.array([F[k, 0], F[k, 1], tau[k] + tc])
-        p = (np.array([fill, s[5]]) - scales["p_mean"]) / scales["p_scale"]
+        p = np.array([fill, s[5]])
+        if p_range is not None:
+            p = np.minimum(np.maximum(p, p_range[0]), p_range[1])
+        p = (p - scales["p_mean"]) / scales["p_scale"]
         o = W @ features(x, u / scales["u"], p)
         x = o[:nx]
         yl = o[nx:] * scales["y"]

@@ -122,14 +122,16 @@ int lpv_create(const lpv_config* cfg, lpv_model** out)
     for (int i = 0; i < 2; ++i) {
         d.pm[i] = 0.f;
         d.inv_ps[i] = 1.f;
+        d.plo[i] = -INFINITY;
+        d.phi[i] = INFINITY;
     }
     bool ok = cudaMalloc(&M->Wp, kWN * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&M->m, kWN * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&M->v, kWN * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&M->grad, kWN * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&M->d_loss, sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&M->stats_part, 256 * 32 * sizeof(double)) == cudaSuccess &&
-              cudaMalloc(&M->stats, 32 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&M->stats_part, 256 * 64 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&M->stats, 64 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&M->gram_part, (size_t)gram_blocks() * 1024 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&M->theta, 32 * 16 * sizeof(double)) == cudaSuccess &&
               cudaMalloc(&M->rho, sizeof(double)) == cudaSuccess &&
@@ -186,6 +188,8 @@ int lpv_set_params(lpv_model* M, const float* W, const float* scales)
         for (int i = 0; i < dm.np; ++i) {
             dm.pm[i] = s[dm.nu + dm.ny + i];
             dm.inv_ps[i] = 1.f / s[dm.nu + dm.ny + dm.np + i];
+            dm.plo[i] = s[dm.nu + dm.ny + 2 * dm.np + i];
+            dm.phi[i] = s[dm.nu + dm.ny + 3 * dm.np + i];
         }
     }
     return SPH_OK;
@@ -209,6 +213,8 @@ int lpv_get_params(const lpv_model* M, float* W, float* scales)
         for (int i = 0; i < d.np; ++i) {
             scales[d.nu + d.ny + i] = d.pm[i];
             scales[d.nu + d.ny + d.np + i] = 1.f / d.inv_ps[i];
+            scales[d.nu + d.ny + 2 * d.np + i] = d.plo[i];
+            scales[d.nu + d.ny + 3 * d.np + i] = d.phi[i];
         }
     }
     return SPH_OK;
@@ -223,8 +229,8 @@ int lpv_normalize(lpv_model* M, const float* u, const float* y, const float* p, 
     Dims& d = M->d;
     const long long n = (long long)n_traj * T;
     LCK(launch_stats(u, y, p, n, d.nu, d.ny, d.np, M->stats_part, M->stats, st));
-    double s[32];
-    LCK(cudaMemcpyAsync(s, M->stats, 32 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    double s[64];
+    LCK(cudaMemcpyAsync(s, M->stats, 64 * sizeof(double), cudaMemcpyDeviceToHost, st));
     LCK(cudaStreamSynchronize(st));
     auto safe = [](double v) { return (v > 1e-30 && std::isfinite(v)) ? v : 1.0; };
     for (int i = 0; i < d.nu; ++i) d.inv_su[i] = (float)(1.0 / safe(std::sqrt(s[i] / n)));
@@ -238,6 +244,8 @@ int lpv_normalize(lpv_model* M, const float* u, const float* y, const float* p, 
         const double var = s[d.nu + d.ny + d.np + i] / n - mean * mean;
         d.pm[i] = (float)mean;
         d.inv_ps[i] = (float)(1.0 / safe(std::sqrt(std::max(var, 0.0))));
+        d.plo[i] = (float)s[32 + i];
+        d.phi[i] = (float)s[32 + d.np + i];
     }
     return SPH_OK;
 }

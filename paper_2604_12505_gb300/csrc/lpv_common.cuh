@@ -21,6 +21,7 @@ struct Dims {
     float inv_su[16];          // 1 / s_u
     float sy[16], inv_sy[16];  // s_y and 1 / s_y
     float pm[2], inv_ps[2];    // scheduling mean, 1 / std
+    float plo[2], phi[2];      // scheduling range of the data (closed-loop clamp)
 };
 
 // 1 where a padded weight is trainable (not padding, not a D block).

@@ -362,8 +362,9 @@ __global__ void __launch_bounds__(128) closed_loop_kernel(const float* __restric
             uu[q][0] = vv[q] ? (float)F[2 * o] : 0.f;
             uu[q][1] = vv[q] ? (float)F[2 * o + 1] : 0.f;
             uu[q][2] = vv[q] ? (float)tau[o] + tc : 0.f;
-            pp[q][0] = d.np > 0 ? (fl[q] - d.pm[0]) * d.inv_ps[0] : 0.f;
-            pp[q][1] = d.np > 1 ? (bs[q][5] - d.pm[1]) * d.inv_ps[1] : 0.f;
+            // scheduling clamped to the range it was identified on
+            pp[q][0] = d.np > 0 ? (fminf(fmaxf(fl[q], d.plo[0]), d.phi[0]) - d.pm[0]) * d.inv_ps[0] : 0.f;
+            pp[q][1] = d.np > 1 ? (fminf(fmaxf(bs[q][5], d.plo[1]), d.phi[1]) - d.pm[1]) * d.inv_ps[1] : 0.f;
         }
         float z[8];
 #pragma unroll

@@ -86,12 +86,17 @@ __global__ void adam_kernel(float* __restrict__ Wp, float* __restrict__ m, float
     Wp[idx] = w - lr * sc * (mm * c1) / (sqrtf(vv * c2) + eps);
 }
 
-// Channel sums over n rows (FP64); block partials, then a fixed-order sum.
+// Channel sums over n rows (FP64) and the range of each scheduling channel;
+// block partials (stride kStatStride: sums at 0.., min at 32.., max at 32 + np..),
+// then a fixed-order combination.
+constexpr int kStatStride = 64;
+
 __global__ void stats_kernel(const float* __restrict__ u, const float* __restrict__ y, const float* __restrict__ p,
                              long long n, int nu, int ny, int np, double* __restrict__ part)
 {
     const int nch = nu + ny + 2 * np;
     double acc[32];
+    float lo[2] = {INFINITY, INFINITY}, hi[2] = {-INFINITY, -INFINITY};
     for (int c = 0; c < nch; ++c) acc[c] = 0.0;
     for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x) {
         for (int c = 0; c < nu; ++c) {
@@ -103,33 +108,62 @@ __global__ void stats_kernel(const float* __restrict__ u, const float* __restric
             acc[nu + c] += x * x;
         }
         for (int c = 0; c < np; ++c) {
-            const double x = p[r * np + c];
+            const float xf = p[r * np + c];
+            const double x = xf;
             acc[nu + ny + c] += x;
             acc[nu + ny + np + c] += x * x;
+            lo[c] = fminf(lo[c], xf);
+            hi[c] = fmaxf(hi[c], xf);
         }
     }
-    __shared__ double sh[32][33];
+    __shared__ double sh[36][33];
     for (int c = 0; c < nch; ++c) {
         double v = acc[c];
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xffffffffu, v, s);
         if ((threadIdx.x & 31) == 0) sh[c][threadIdx.x >> 5] = v;
     }
+    for (int c = 0; c < np; ++c) {
+        float a = lo[c], b = hi[c];
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) {
+            a = fminf(a, __shfl_down_sync(0xffffffffu, a, s));
+            b = fmaxf(b, __shfl_down_sync(0xffffffffu, b, s));
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sh[32 + c][threadIdx.x >> 5] = a;
+            sh[32 + np + c][threadIdx.x >> 5] = b;
+        }
+    }
     __syncthreads();
+    const int nw = (int)(blockDim.x >> 5);
     if (threadIdx.x < nch) {
         double v = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += sh[threadIdx.x][w];
-        part[blockIdx.x * 32 + threadIdx.x] = v;
+        for (int w = 0; w < nw; ++w) v += sh[threadIdx.x][w];
+        part[blockIdx.x * kStatStride + threadIdx.x] = v;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 32 + 2 * np) {
+        const bool is_lo = threadIdx.x < 32 + np;
+        double v = sh[threadIdx.x][0];
+        for (int w = 1; w < nw; ++w) v = is_lo ? fmin(v, sh[threadIdx.x][w]) : fmax(v, sh[threadIdx.x][w]);
+        part[blockIdx.x * kStatStride + threadIdx.x] = v;
     }
 }
 
-__global__ void stats_final_kernel(const double* __restrict__ part, int n_blocks, int nch, double* __restrict__ stats)
+__global__ void stats_final_kernel(const double* __restrict__ part, int n_blocks, int nch, int np,
+                                   double* __restrict__ stats)
 {
     const int c = threadIdx.x;
-    if (c >= nch) return;
-    double v = 0.0;
-    for (int b = 0; b < n_blocks; ++b) v += part[b * 32 + c];
-    stats[c] = v;
+    if (c < nch) {
+        double v = 0.0;
+        for (int b = 0; b < n_blocks; ++b) v += part[b * kStatStride + c];
+        stats[c] = v;
+    } else if (c >= 32 && c < 32 + 2 * np) {
+        const bool is_lo = c < 32 + np;
+        double v = part[c];
+        for (int b = 1; b < n_blocks; ++b)
+            v = is_lo ? fmin(v, part[b * kStatStride + c]) : fmax(v, part[b * kStatStride + c]);
+        stats[c] = v;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -517,7 +551,7 @@ cudaError_t launch_stats(const float* u, const float* y, const float* p, long lo
                          double* part, double* stats, cudaStream_t st)
 {
     stats_kernel<<<256, 256, 0, st>>>(u, y, p, n, nu, ny, np, part);
-    stats_final_kernel<<<1, 32, 0, st>>>(part, 256, nu + ny + 2 * np, stats);
+    stats_final_kernel<<<1, kStatStride, 0, st>>>(part, 256, nu + ny + 2 * np, np, stats);
     return cudaGetLastError();
 }
 

@@ -57,7 +57,7 @@ class Model:
         self._h = _handle
         c = self.cfg
         self.shape_W = (1 + c["n_p"], c["n_x"] + c["n_y"], c["n_x"] + c["n_u"])
-        self.n_scales = c["n_u"] + c["n_y"] + 2 * c["n_p"]
+        self.n_scales = c["n_u"] + c["n_y"] + 4 * c["n_p"]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -40,7 +40,8 @@ def _data(rng, n, T, n_p=NP):
 
 
 def _unit_scales(n_p=NP):
-    return np.concatenate([np.ones(NU), np.ones(NY), np.zeros(n_p), np.ones(n_p)]).astype(np.float32)
+    return np.concatenate([np.ones(NU), np.ones(NY), np.zeros(n_p), np.ones(n_p), np.full(n_p, -np.inf),
+                           np.full(n_p, np.inf)]).astype(np.float32)
 
 
 def _model(n_p=NP, **kw):
@@ -132,7 +133,10 @@ def test_normalisation_statistics():
     np.testing.assert_allclose(s[:NU], np.sqrt((u ** 2).mean(axis=(0, 1))), rtol=1e-5)
     np.testing.assert_allclose(s[NU:NU + NY], np.sqrt((y ** 2).mean(axis=(0, 1))), rtol=1e-5)
     np.testing.assert_allclose(s[NU + NY:NU + NY + NP], p.mean(axis=(0, 1)), rtol=1e-5, atol=1e-6)
-    np.testing.assert_allclose(s[NU + NY + NP:], p.std(axis=(0, 1)), rtol=1e-4)
+    np.testing.assert_allclose(s[NU + NY + NP:NU + NY + 2 * NP], p.std(axis=(0, 1)), rtol=1e-4)
+    p32 = p.astype(np.float32)
+    np.testing.assert_array_equal(s[NU + NY + 2 * NP:NU + NY + 3 * NP], p32.min(axis=(0, 1)))
+    np.testing.assert_array_equal(s[NU + NY + 3 * NP:], p32.max(axis=(0, 1)))
 
 
 @pytest.mark.parametrize("n_traj,T", [(37, 40), (16, 7)])
@@ -160,7 +164,8 @@ def test_free_run_prediction_matches_oracle():
     rng = np.random.default_rng(3)
     Wt = _stable_W(rng)
     u, p = _data(rng, 33, 300)
-    scales = np.concatenate([[2.0, 3.0, 0.5], [10.0, 20.0, 1.5, 0.1], [0.1, -0.2], [0.5, 2.0]]).astype(np.float32)
+    scales = np.concatenate([[2.0, 3.0, 0.5], [10.0, 20.0, 1.5, 0.1], [0.1, -0.2], [0.5, 2.0],
+                             [-np.inf, -np.inf], [np.inf, np.inf]]).astype(np.float32)
     m = _model()
     m.set_params(Wt.reshape(NX + NY, 1 + NP, NX + NU).transpose(1, 0, 2), scales)
     W32 = m.get_params()[0].transpose(1, 0, 2).reshape(NX + NY, -1).astype(np.float64)
@@ -177,7 +182,9 @@ def test_closed_loop_matches_oracle():
     rng = np.random.default_rng(4)
     Wt = _stable_W(rng, scale=0.05)
     B, T = 37, 200
-    scales = np.array([20.0, 20.0, 2.0, 30.0, 30.0, 3.0, 0.05, 0.5, 0.0, 0.2, 0.05], dtype=np.float32)
+    # the angular-rate range is narrower than the runs reach: the clamp is exercised
+    scales = np.array([20.0, 20.0, 2.0, 30.0, 30.0, 3.0, 0.05, 0.5, 0.0, 0.2, 0.05, 0.2, -0.01, 0.8, 0.01],
+                      dtype=np.float32)
     m = _model()
     m.set_params(Wt.reshape(NX + NY, 1 + NP, NX + NU).transpose(1, 0, 2), scales)
     W32 = m.get_params()[0].transpose(1, 0, 2).reshape(NX + NY, -1).astype(np.float64)
@@ -187,14 +194,18 @@ def test_closed_loop_matches_oracle():
     fill = rng.uniform(0.2, 0.8, size=B)
     body = dict(m=500.0, J=50.0, Ts=0.005, n_sub=10, ctrl_omega=0.2 * np.pi, ctrl_xi=0.7)
     out = m.simulate(F, tau, ref, fill, body).cpu().numpy()
+    clamped = 0
     sc = dict(u=scales[:3].astype(np.float64), y=scales[3:7].astype(np.float64),
               p_mean=scales[7:9].astype(np.float64), p_scale=scales[9:11].astype(np.float64))
     for b in range(B):
         o = L.closed_loop(W32, NX, sc, body, fill[b], F[b], tau[b], ref[b], body["Ts"], body["n_sub"],
-                          dict(omega=body["ctrl_omega"], xi=body["ctrl_xi"]))
+                          dict(omega=body["ctrl_omega"], xi=body["ctrl_xi"]),
+                          p_range=(scales[11:13].astype(np.float64), scales[13:15].astype(np.float64)))
+        clamped += np.abs(o[:, 5]).max() > 0.01
         for cols in ([0, 1], [2], [3, 4], [5]):
             den = np.linalg.norm(o[:, cols], axis=1).max()
             assert np.linalg.norm(out[b][:, cols] - o[:, cols], axis=1).max() <= 1e-3 * den
+    assert clamped > 0
 
 
 def test_training_reduces_loss_and_scheduling_gains_over_lti():
