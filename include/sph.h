@@ -138,6 +138,7 @@ int sph_ghosts_body(const sph_sim* sim, int32_t b, double* gB_host);
  * frame, tanks concatenated, particles of a tank in builder order.  body:
  * float64 [B, 6] rows (r_x, r_y, theta, rdot_x, rdot_y, thetadot).
  * sph_set_state re-bins the fluid; it also clears the held controller torque.
+ * xv may be NULL when the handle holds no fluid particles (every tank empty).
  */
 int sph_get_state(sph_sim* sim, float* xv, double* body, void* stream);
 int sph_set_state(sph_sim* sim, const float* xv, const double* body, void* stream);

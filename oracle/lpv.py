@@ -209,7 +209,7 @@ def adam_step(theta, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
 def closed_loop(W, nx, scales, body, fill, F, tau, theta_ref, Ts, n_sub, pd, p_range=None):
     """One closed-loop run at the sampling period Ts (Section 5.1.1):
       tau_c,k = J w^2 (theta_ref_k - theta_k) - 2 xi J w thetadot_k   (Eq. 28, ZOH)
-      u_k = [F_x, F_y, tau + tau_c],  p_k = [fill, thetadot_k]
+      u_k = [F_x, F_y, tau + tau_c],  p_k = [fill, thetadot_k][:n_p]
       surrogate (normalised units): y_k = C(p) x_k, x_{k+1} = A(p) x_k + B(p) u_k
       sloshing loads [F_bx, F_by, T_b] = y_k[:3] * y_scale[:3]
       body (Eq. 20 with the loads held over the period): n_sub kick-then-drift
@@ -226,11 +226,12 @@ def closed_loop(W, nx, scales, body, fill, F, tau, theta_ref, Ts, n_sub, pd, p_r
     s = np.zeros(6)   # r_x r_y theta v_x v_y omega
     out = np.zeros((T, 6))
     dt = Ts / n_sub
+    n_p = W.shape[1] // (nx + 3) - 1
     for k in range(T):
         out[k] = s
         tc = Jc * w * w * (theta_ref[k] - s[2]) - 2.0 * xi * Jc * w * s[5]
         u = np.array([F[k, 0], F[k, 1], tau[k] + tc])
-        p = np.array([fill, s[5]])
+        p = np.array([fill, s[5]])[:n_p]
         if p_range is not None:
             p = np.minimum(np.maximum(p, p_range[0]), p_range[1])
         p = (p - scales["p_mean"]) / scales["p_scale"]

@@ -514,7 +514,7 @@ int sph_get_state(sph_sim* sim, float* xv, double* body, void* stream)
 
 int sph_set_state(sph_sim* sim, const float* xv, const double* body, void* stream)
 {
-    if (!sim || !xv || !body) return fail(SPH_E_INVAL, "sph_set_state: NULL argument");
+    if (!sim || !body || (!xv && sim->n_f_total > 0)) return fail(SPH_E_INVAL, "sph_set_state: NULL argument");
     cudaStream_t st = (cudaStream_t)stream;
     const int buf = (int)(sim->host_step & 1);
     CK(cudaMemsetAsync(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int), st));

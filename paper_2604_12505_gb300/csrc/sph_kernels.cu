@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
     __shared__ Stage<TX, TY, false, TAN> sm;
     pdl_trigger();
     const int4 td = S.tiles[blockIdx.x];
-    const TankDev& T = S.tank[td.x];
+    const TankDev T = S.tank[td.x];  // by value: the constants live in registers
     const int cx0 = td.y, cy0 = td.z;
     pdl_wait();
     const int buf = (int)(S.run->step & 1), nbuf = buf ^ 1;
@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
     pdl_trigger();
     const int4 td = S.tiles[blockIdx.x];
     const int tank = td.x;
-    const TankDev& T = S.tank[tank];
+    const TankDev T = S.tank[tank];  // by value: the constants live in registers
     const int cx0 = td.y, cy0 = td.z;
     pdl_wait();
     const long long step = S.run->step;
