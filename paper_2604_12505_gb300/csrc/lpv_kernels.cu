@@ -107,15 +107,43 @@ __device__ __forceinline__ void load_fwd_frags(const float* __restrict__ Wp, uin
 __device__ __forceinline__ void load_p(const Dims& d, const float* __restrict__ p, int r, bool valid, int T, int k,
                                        float* pp)
 {
-    pp[0] = pp[1] = 0.f;
-    if (!valid) return;
-    for (int j = 0; j < d.np; ++j) pp[j] = (p[((size_t)r * T + k) * d.np + j] - d.pm[j]) * d.inv_ps[j];
+    const size_t o = ((size_t)r * T + k) * d.np;
+    pp[0] = (valid && d.np > 0) ? (p[o] - d.pm[0]) * d.inv_ps[0] : 0.f;
+    pp[1] = (valid && d.np > 1) ? (p[o + 1] - d.pm[1]) * d.inv_ps[1] : 0.f;
+}
+
+// Inputs of one step that a thread owns: the scheduling of its two
+// trajectories and its feature (u) and output (y) columns, normalised.
+struct StepIn {
+    float p0[2], p1[2];
+    float uz[8];  // u part of z at the thread's 8 columns (0 elsewhere)
+    float yv[8];  // y at the thread's output columns (0 elsewhere; loss only)
+};
+
+template <bool WANT_Y>
+__device__ __forceinline__ void load_step(const Dims& d, const float* __restrict__ u, const float* __restrict__ p,
+                                          const float* __restrict__ y, int r0, int r1, bool v0, bool v1, int T, int k,
+                                          int t, StepIn& in)
+{
+    load_p(d, p, r0, v0, T, k, in.p0);
+    load_p(d, p, r1, v1, T, k, in.p1);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        const int c = scol(i, t);
+        const int r = srow(i) ? r1 : r0;
+        const bool v = srow(i) ? v1 : v0;
+        in.uz[i] = (v && c >= d.nx && c < d.nx + d.nu)
+                       ? u[((size_t)r * T + k) * d.nu + (c - d.nx)] * d.inv_su[c - d.nx] : 0.f;
+        in.yv[i] = (WANT_Y && v && c >= d.nx && c < d.nx + d.ny)
+                       ? y[((size_t)r * T + k) * d.ny + (c - d.nx)] * d.inv_sy[c - d.nx] : 0.f;
+    }
 }
 
 // Free-run simulation of 16 trajectories per warp.  MODE 0 writes the
 // prediction (physical units); MODE 1 accumulates the squared error of the
 // normalised outputs and records, per step, x_k and dJ/dy_k for the
 // backward pass in hist[traj][k][16] (state columns, then output columns).
+// The inputs of step k + 1 are loaded while step k's products run.
 template <int MODE>
 __global__ void __launch_bounds__(128) fwd_kernel(const float* __restrict__ Wp, Dims d, const float* __restrict__ u,
                                                   const float* __restrict__ p, const float* __restrict__ y, int n_traj,
@@ -130,29 +158,21 @@ __global__ void __launch_bounds__(128) fwd_kernel(const float* __restrict__ Wp, 
     load_fwd_frags(Wp, bhi, blo, d.nkt, g, t);
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // x_0 = 0
     float lsum_f = 0.f;                     // widened to FP64 once, after the loop
+    StepIn cur;
+    load_step<MODE == 1>(d, u, p, y, r0, r1, v0, v1, T, 0, t, cur);
     for (int k = 0; k < T; ++k) {
-        float z[8], pp0[2], pp1[2];
-        load_p(d, p, r0, v0, T, k, pp0);
-        load_p(d, p, r1, v1, T, k, pp1);
+        StepIn nxt;
+        load_step<MODE == 1>(d, u, p, y, r0, r1, v0, v1, T, k + 1 < T ? k + 1 : k, t, nxt);
+        float z[8];
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int c = scol(i, t);
-            const int r = srow(i) ? r1 : r0;
-            const bool v = srow(i) ? v1 : v0;
-            if (c < d.nx)
-                z[i] = s[i];
-            else if (c < d.nx + d.nu)
-                z[i] = v ? u[((size_t)r * T + k) * d.nu + (c - d.nx)] * d.inv_su[c - d.nx] : 0.f;
-            else
-                z[i] = 0.f;
-        }
+        for (int i = 0; i < 8; ++i) z[i] = (scol(i, t) < d.nx) ? s[i] : cur.uz[i];
         uint32_t ahi[kMaxKT][4], alo[kMaxKT][4];
         afrag(z, ahi[0], alo[0]);
 #pragma unroll
         for (int kt = 1; kt < kMaxKT; ++kt) {
             float zs[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) zs[i] = z[i] * (srow(i) ? pp1[kt - 1] : pp0[kt - 1]);
+            for (int i = 0; i < 8; ++i) zs[i] = z[i] * (srow(i) ? cur.p1[kt - 1] : cur.p0[kt - 1]);
             afrag(zs, ahi[kt], alo[kt]);
         }
         float D[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -169,13 +189,14 @@ __global__ void __launch_bounds__(128) fwd_kernel(const float* __restrict__ Wp, 
                 if (MODE == 0) {
                     y_out[((size_t)r * T + k) * d.ny + q] = D[i] * d.sy[q];
                 } else {
-                    const float res = D[i] - y[((size_t)r * T + k) * d.ny + q] * d.inv_sy[q];
+                    const float res = D[i] - cur.yv[i];
                     lsum_f = fmaf(res, res, lsum_f);
                     hist[((size_t)r * T + k) * 16 + c] = grad_scale * res;
                 }
             }
             s[i] = (c < d.nx) ? D[i] : 0.f;
         }
+        cur = nxt;
     }
     if (MODE == 1) {
         double lsum = (double)lsum_f;
@@ -228,23 +249,32 @@ __global__ void __launch_bounds__(32 * kBwdWarps) bwd_kernel(const float* __rest
     float gacc[6][4];
 #pragma unroll
     for (int nt = 0; nt < 6; ++nt) gacc[nt][0] = gacc[nt][1] = gacc[nt][2] = gacc[nt][3] = 0.f;
-    for (int k = T - 1; k >= 0; --k) {
-        float G[8], z[8], pp0[2], pp1[2];
-        load_p(d, p, r0, v0, T, k, pp0);
-        load_p(d, p, r1, v1, T, k, pp1);
+    // step inputs: scheduling, recorded history (x_k | dJ/dy_k) and u; those of
+    // step k - 1 are loaded while step k's products run
+    auto fetch = [&](int k, float* pa0, float* pa1, float* hv, float* uz) {
+        load_p(d, p, r0, v0, T, k, pa0);
+        load_p(d, p, r1, v1, T, k, pa1);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int c = scol(i, t);
             const int r = srow(i) ? r1 : r0;
             const bool v = srow(i) ? v1 : v0;
-            const float hv = (v && c < d.nx + d.ny) ? hist[((size_t)r * T + k) * 16 + c] : 0.f;
-            G[i] = (c < d.nx) ? lam[i] : hv;
-            if (c < d.nx)
-                z[i] = hv;  // x_k
-            else if (c < d.nx + d.nu)
-                z[i] = v ? u[((size_t)r * T + k) * d.nu + (c - d.nx)] * d.inv_su[c - d.nx] : 0.f;
-            else
-                z[i] = 0.f;
+            hv[i] = (v && c < d.nx + d.ny) ? hist[((size_t)r * T + k) * 16 + c] : 0.f;
+            uz[i] = (v && c >= d.nx && c < d.nx + d.nu)
+                        ? u[((size_t)r * T + k) * d.nu + (c - d.nx)] * d.inv_su[c - d.nx] : 0.f;
+        }
+    };
+    float cp0[2], cp1[2], chv[8], cuz[8];
+    fetch(T - 1, cp0, cp1, chv, cuz);
+    for (int k = T - 1; k >= 0; --k) {
+        float np0[2], np1[2], nhv[8], nuz[8];
+        fetch(k > 0 ? k - 1 : 0, np0, np1, nhv, nuz);
+        float G[8], z[8], pp0[2] = {cp0[0], cp0[1]}, pp1[2] = {cp1[0], cp1[1]};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int c = scol(i, t);
+            G[i] = (c < d.nx) ? lam[i] : chv[i];
+            z[i] = (c < d.nx) ? chv[i] : cuz[i];  // x_k, u_k, 0
         }
         // gw = G W
         uint32_t ghi[4], glo[4];
@@ -297,6 +327,15 @@ __global__ void __launch_bounds__(32 * kBwdWarps) bwd_kernel(const float* __rest
             mma16816(gacc[nt], alo, b0h, b1h);
         }
         __syncwarp();
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            chv[i] = nhv[i];
+            cuz[i] = nuz[i];
+        }
+        cp0[0] = np0[0];
+        cp0[1] = np0[1];
+        cp1[0] = np1[0];
+        cp1[1] = np1[1];
     }
     // gacc[nt]: (o = g, f = 8 nt + 2t), (g, +1), (g + 8, 2t), (g + 8, 2t + 1)
     float* out = gpart + (size_t)wid * kWN;
@@ -349,7 +388,23 @@ __global__ void __launch_bounds__(128) closed_loop_kernel(const float* __restric
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     float bs[2][6] = {{0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0}};  // r_x r_y theta v_x v_y omega
     const float fl[2] = {vv[0] ? (float)fill[rr[0]] : 0.f, vv[1] ? (float)fill[rr[1]] : 0.f};
+    // inputs of a period (F_x, F_y, tau, theta_ref) for the two rows; those of
+    // period k + 1 are loaded while period k runs
+    auto fetch = [&](int k, float (*in)[4]) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const size_t o = (size_t)rr[q] * T + k;
+            in[q][0] = vv[q] ? (float)F[2 * o] : 0.f;
+            in[q][1] = vv[q] ? (float)F[2 * o + 1] : 0.f;
+            in[q][2] = vv[q] ? (float)tau[o] : 0.f;
+            in[q][3] = vv[q] ? (float)ref[o] : 0.f;
+        }
+    };
+    float cin[2][4];
+    fetch(0, cin);
     for (int k = 0; k < T; ++k) {
+        float nin[2][4];
+        fetch(k + 1 < T ? k + 1 : k, nin);
         float uu[2][3], pp[2][2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
@@ -358,10 +413,10 @@ __global__ void __launch_bounds__(128) closed_loop_kernel(const float* __restric
 #pragma unroll
                 for (int j = 0; j < 6; ++j) out[o * 6 + j] = bs[q][j];
             }
-            const float tc = vv[q] ? bp.kp * ((float)ref[o] - bs[q][2]) - bp.kd * bs[q][5] : 0.f;
-            uu[q][0] = vv[q] ? (float)F[2 * o] : 0.f;
-            uu[q][1] = vv[q] ? (float)F[2 * o + 1] : 0.f;
-            uu[q][2] = vv[q] ? (float)tau[o] + tc : 0.f;
+            const float tc = vv[q] ? bp.kp * (cin[q][3] - bs[q][2]) - bp.kd * bs[q][5] : 0.f;
+            uu[q][0] = cin[q][0];
+            uu[q][1] = cin[q][1];
+            uu[q][2] = vv[q] ? cin[q][2] + tc : 0.f;
             // scheduling clamped to the range it was identified on
             pp[q][0] = d.np > 0 ? (fminf(fmaxf(fl[q], d.plo[0]), d.phi[0]) - d.pm[0]) * d.inv_ps[0] : 0.f;
             pp[q][1] = d.np > 1 ? (fminf(fmaxf(bs[q][5], d.plo[1]), d.phi[1]) - d.pm[1]) * d.inv_ps[1] : 0.f;
@@ -401,6 +456,10 @@ __global__ void __launch_bounds__(128) closed_loop_kernel(const float* __restric
         }
 #pragma unroll
         for (int i = 0; i < 8; ++i) s[i] = (scol(i, t) < d.nx) ? D[i] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) cin[q][j] = nin[q][j];
     }
 }
 
