@@ -230,6 +230,30 @@ int sph_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv0, 
             double* y_out, double* dy_out, float* dxv_out, double* dbody_out, void* stream);
 
 /*
+ * Reverse-mode (adjoint) derivative of K steps: the transpose of the map
+ * sph_jvp linearises (Section 3.5, Jacobians of the simulator), no
+ * controller, the neighbour set of each step frozen.  From the current state
+ * and the input u, given the adjoints of that K-step call's samples and of
+ * the final state, computes the adjoints of the initial state and of u:
+ *  u          float64 [B, K, 3] input (NULL: zero), device
+ *  ybar       float64 [B, n_samples, SPH_NY] adjoint of the samples sph_step(K)
+ *             would record from the current step (NULL: zero)
+ *  xvbar_K    float32 [N, 4] adjoint of the final fluid state (NULL: zero)
+ *  bodybar_K  float64 [B, 6] adjoint of the final body state (NULL: zero)
+ *  xvbar0     float32 [N, 4] out: adjoint of the initial fluid state (NULL: skip)
+ *  bodybar0   float64 [B, 6] out: adjoint of the initial body state (NULL: skip)
+ *  ubar       float64 [B, K, 3] out: adjoint of u (NULL: skip)
+ * The forward pass keeps a checkpoint every checkpoint_every steps; the
+ * reverse sweep recomputes each segment from its checkpoint and runs the
+ * adjoint kernels on 4x4 tiles (device memory of about K / checkpoint_every +
+ * checkpoint_every states, allocated for the call).  The simulator is left at
+ * state K, as after sph_jvp.  Blocks until done.
+ */
+int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const float* xvbar_K,
+            const double* bodybar_K, float* xvbar0, double* bodybar0, double* ubar, int32_t checkpoint_every,
+            void* stream);
+
+/*
  * Kernel-shape control.  tile = 0 lets the library pick; otherwise one of
  * the codes 1..SPH_TILE_COUNT (cell blocks 2x2, 4x2, 4x4, 8x4, 8x8).
  * sph_autotune times every shape on the current state for `steps` steps,

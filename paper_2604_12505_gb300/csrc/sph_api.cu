@@ -113,6 +113,29 @@ int dalloc(T** p, size_t n)
     return SPH_OK;
 }
 
+// Device buffers of one call, freed on every return path.
+struct DevScratch {
+    std::vector<void*> ptrs;
+    template <class T>
+    int get(T** p, size_t n)
+    {
+        const int rc = dalloc(p, n);
+        if (rc == SPH_OK) ptrs.push_back((void*)*p);
+        return rc;
+    }
+    ~DevScratch()
+    {
+        for (void* q : ptrs) cudaFree(q);
+    }
+};
+
+// Rows [k0, k0 + n) of u [B, K, 3] into dst [B, n, 3].
+cudaError_t slice_u(double* dst, const double* u, int B, int K, int k0, int n, cudaStream_t st)
+{
+    return cudaMemcpy2DAsync(dst, 3 * sizeof(double) * n, u + 3ll * k0, 3 * sizeof(double) * K,
+                             3 * sizeof(double) * n, B, cudaMemcpyDeviceToDevice, st);
+}
+
 }  // namespace
 
 namespace sph {
@@ -632,6 +655,100 @@ int sph_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv0, 
         float* tx = dxv_out ? dxv_out : sim->d_scratch_xv;
         CK(launch_tangent_state(S, nullptr, tx, nullptr, dbody_out, sim->n_cells_total, (int)(sim->host_step & 1), st));
     }
+    return SPH_OK;
+}
+
+int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const float* xvbar_K,
+            const double* bodybar_K, float* xvbar0, double* bodybar0, double* ubar, int32_t checkpoint_every,
+            void* stream)
+{
+    if (!sim || K < 0 || checkpoint_every < 1) return fail(SPH_E_INVAL, "sph_vjp: bad argument");
+    for (int b = 1; b < sim->B; ++b)
+        if (sim->tanks[b].p.outer_every != sim->tanks[0].p.outer_every)
+            return fail(SPH_E_UNSUPPORTED, "sph_vjp: tanks of a batch must share outer_every");
+    cudaStream_t st = (cudaStream_t)stream;
+    const int B = sim->B, N = sim->n_f_total, C = checkpoint_every;
+    const long long step0 = sim->host_step;
+    const int oe = sim->tanks[0].p.outer_every > 0 ? sim->tanks[0].p.outer_every : 1;
+    const int n_seg = (K + C - 1) / C;
+    const size_t nxv = 4 * (size_t)N;
+    DevScratch mem;
+    float4 *adj0 = nullptr, *adj1 = nullptr;
+    float *rhob = nullptr, *fbar = nullptr, *part = nullptr, *ck_xv = nullptr, *seg_xv = nullptr, *fin_xv = nullptr;
+    double *bbar = nullptr, *bpart = nullptr, *ck_b = nullptr, *seg_b = nullptr, *fin_b = nullptr, *us = nullptr;
+    const int code = adjoint_tile_code();
+    int rc = mem.get(&adj0, N) | mem.get(&adj1, N) | mem.get(&rhob, N) | mem.get(&fbar, 8 * (size_t)B) |
+             mem.get(&part, 2 * (size_t)sim->max_tiles * 12) | mem.get(&bbar, 6 * (size_t)B) |
+             mem.get(&bpart, 6 * (size_t)B) | mem.get(&ck_xv, nxv * (n_seg ? n_seg : 1)) |
+             mem.get(&ck_b, 6 * (size_t)B * (n_seg ? n_seg : 1)) | mem.get(&seg_xv, nxv * C) |
+             mem.get(&seg_b, 6 * (size_t)B * C) | mem.get(&fin_xv, nxv) | mem.get(&fin_b, 6 * (size_t)B) |
+             mem.get(&us, 3 * (size_t)B * C);
+    if (rc) return SPH_E_NOMEM;
+    // adjoint of the final state
+    if (xvbar_K) CK(cudaMemcpyAsync(adj0, xvbar_K, nxv * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemsetAsync(adj0, 0, nxv * sizeof(float), st));
+    if (bodybar_K) CK(cudaMemcpyAsync(bbar, bodybar_K, 6 * B * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    else CK(cudaMemsetAsync(bbar, 0, 6 * B * sizeof(double), st));
+    // forward: a checkpoint every C steps, then the final state
+    for (int sgi = 0; sgi < n_seg; ++sgi) {
+        const int k0 = sgi * C, n = std::min(C, K - k0);
+        if ((rc = sph_get_state(sim, ck_xv + nxv * sgi, ck_b + 6ll * B * sgi, stream))) return rc;
+        if (u) CK(slice_u(us, u, B, K, k0, n, st));
+        if ((rc = sph_step(sim, u ? us : nullptr, n, nullptr, nullptr, stream))) return rc;
+    }
+    if ((rc = sph_get_state(sim, fin_xv, fin_b, stream))) return rc;
+    AdjDev A{};
+    A.rhobar = rhob;
+    A.bbar = bbar;
+    A.bbar_part = bpart;
+    A.fbar = fbar;
+    A.part = part;
+    A.max_tiles = sim->max_tiles;
+    A.ybar = ybar;
+    int32_t ns = 0;
+    {   // samples of the forward call
+        long long first = (step0 + oe - 1) / oe, last = (step0 + K + oe - 1) / oe;
+        ns = (int32_t)(last - first);
+    }
+    A.ybar_stride = (long long)ns * SPH_NY;
+    A.ubar = ubar;
+    A.ubar_stride = 3ll * K;
+    const SimDev S = sim->dev(code);
+    float4* cur = adj0;
+    float4* nxt = adj1;
+    for (int sgi = n_seg - 1; sgi >= 0; --sgi) {
+        const int k0 = sgi * C, n1 = std::min(K, k0 + C);
+        // recompute the states of the segment from its checkpoint
+        sim->host_step = step0 + k0;
+        CK(launch_set_step(sim->d_run, sim->host_step, st));
+        if ((rc = sph_set_state(sim, ck_xv + nxv * sgi, ck_b + 6ll * B * sgi, stream))) return rc;
+        for (int k = k0; k < n1; ++k) {
+            if ((rc = sph_get_state(sim, seg_xv + nxv * (k - k0), seg_b + 6ll * B * (k - k0), stream))) return rc;
+            if (k + 1 < n1) {
+                if (u) CK(slice_u(us, u, B, K, k, 1, st));
+                if ((rc = sph_step(sim, u ? us : nullptr, 1, nullptr, nullptr, stream))) return rc;
+            }
+        }
+        for (int k = n1 - 1; k >= k0; --k) {
+            sim->host_step = step0 + k;
+            CK(launch_set_step(sim->d_run, sim->host_step, st));
+            if ((rc = sph_set_state(sim, seg_xv + nxv * (k - k0), seg_b + 6ll * B * (k - k0), stream))) return rc;
+            const long long g = step0 + k;
+            A.k = k;
+            A.row = (g % oe == 0) ? (int)(g / oe - (step0 + oe - 1) / oe) : -1;
+            A.in = cur;
+            A.out = nxt;
+            CK(launch_adjoint_step(S, A, sim->n_tiles[code], st));
+            std::swap(cur, nxt);
+        }
+    }
+    if (xvbar0) CK(cudaMemcpyAsync(xvbar0, cur, nxv * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (bodybar0) CK(cudaMemcpyAsync(bodybar0, bbar, 6 * B * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // leave the simulator at the final state, as sph_jvp does
+    sim->host_step = step0 + K;
+    CK(launch_set_step(sim->d_run, sim->host_step, st));
+    if ((rc = sph_set_state(sim, fin_xv, fin_b, stream))) return rc;
+    CK(cudaStreamSynchronize(st));  // the scratch buffers are freed on return
     return SPH_OK;
 }
 

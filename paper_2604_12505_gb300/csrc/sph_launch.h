@@ -23,4 +23,27 @@ cudaError_t launch_tangent_state(const SimDev& S, const float* txv_in, float* tx
                                  double* tb_out, int n_cells_total, int buf, cudaStream_t st);
 cudaError_t launch_set_run(RunDev* run, const RunDev& desc, cudaStream_t st);
 
+// Reverse-mode step (sph_adjoint.cu).  Adjoint arrays are indexed by particle
+// index (the order of sph_get_state); body adjoints are (r_x, r_y, theta,
+// rdot_x, rdot_y, thetadot).
+struct AdjDev {
+    const float4* in;        // [N] adjoint of (x, v) after the step
+    float4* out;             // [N] adjoint of (x, v) before the step
+    float* rhobar;           // [N] density adjoint (work)
+    double* bbar;            // [B * 6] body adjoint: after the step on entry, before it on exit
+    double* bbar_part;       // [B * 6] work: the integration part
+    float* fbar;             // [B * 8] work: F_b, T_b and centre-of-mass adjoints of the step
+    float* part;             // [2][max_tiles][12] work: per-tile body partials
+    int max_tiles;
+    const double* ybar;      // [B, n_samples, SPH_NY] sample adjoints (NULL: 0)
+    long long ybar_stride;   // doubles between tanks
+    double* ubar;            // [B, K, 3] input adjoints (NULL: not written)
+    long long ubar_stride;
+    int k;                   // step index within the call
+    int row;                 // sample row of this step, -1: not sampled
+};
+int adjoint_tile_code();
+cudaError_t launch_adjoint_step(const SimDev& S, const AdjDev& A, int n_tiles, cudaStream_t st);
+cudaError_t launch_set_step(RunDev* run, long long step, cudaStream_t st);
+
 }  // namespace sph

@@ -169,6 +169,24 @@ class Sim:
         self.steps_done += K
         return y, dy, dxv, dbody
 
+    def vjp(self, K: int, u=None, ybar=None, xvbar=None, bodybar=None, checkpoint_every: int = 10, stream=None):
+        """Reverse-mode derivative of K steps from the current state (sph_vjp).
+        ybar: adjoint of the samples [B, n, 11]; xvbar [N, 4], bodybar [B, 6]:
+        adjoints of the final state.  Returns (xvbar0 [N, 4], bodybar0 [B, 6],
+        ubar [B, K, 3]) and leaves the simulator at state K."""
+        u = None if u is None else _dev(u, torch.float64).reshape(self.B, K, 3)
+        ns = self.samples_for(K)
+        ybar = None if ybar is None else _dev(ybar, torch.float64).reshape(self.B, ns, NY)
+        xvbar = None if xvbar is None else _dev(xvbar, torch.float32).reshape(self.n_total, 4)
+        bodybar = None if bodybar is None else _dev(bodybar, torch.float64).reshape(self.B, 6)
+        xb0 = torch.empty((self.n_total, 4), dtype=torch.float32, device="cuda")
+        bb0 = torch.empty((self.B, 6), dtype=torch.float64, device="cuda")
+        ub = torch.empty((self.B, K, 3), dtype=torch.float64, device="cuda")
+        check(lib().sph_vjp(self._h, _ptr(u), K, _ptr(ybar), _ptr(xvbar), _ptr(bodybar), _ptr(xb0), _ptr(bb0),
+                            _ptr(ub), checkpoint_every, _stream(stream)), "sph_vjp")
+        self.steps_done += K
+        return xb0, bb0, ub
+
     def eval(self, u=None, stream=None):
         """Algorithm 1 on the current state without stepping."""
         N = self.n_total
