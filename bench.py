@@ -249,6 +249,22 @@ def surrogate(size: str) -> dict:
     }
 
 
+def combine_ranks(seconds: float, units: float, device) -> tuple[float, float]:
+    """Whole-job time and work of independent replicas: the maximum time and
+    the summed units over the ranks of the default process group (the
+    identity on a single process)."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return seconds, units
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    w = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(w, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(w.item())
+
+
 def run_ours(a):
     import torch
     import torch.distributed as dist
@@ -313,13 +329,7 @@ def run_ours(a):
     sim.check()
     T = sum(ms) / 1000.0
     pairs = c1 - c0
-    t_red = torch.tensor([T, float(pairs)], dtype=torch.float64, device="cuda")
-    if world > 1:
-        tmax = t_red[:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        psum = t_red[1:].clone()
-        dist.all_reduce(psum, op=dist.ReduceOp.SUM)
-        T, pairs = float(tmax.item()), float(psum.item())
+    T, pairs = combine_ranks(T, float(pairs), "cuda")
     value = pairs / T
 
     # end to end through the public API with host buffers: pinned input copy
@@ -342,11 +352,8 @@ def run_ours(a):
         e2e_ms.append(e0.elapsed_time(e1))
         flush.zero_()
     ce1 = sim.pair_count()
-    e2e_val = (ce1 - ce0) / (sum(e2e_ms) / 1000.0)
-    if world > 1:
-        tt = torch.tensor([sum(e2e_ms) / 1000.0], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_val = (ce1 - ce0) * world / float(tt.item())
+    e2e_t, e2e_pairs = combine_ranks(sum(e2e_ms) / 1000.0, float(ce1 - ce0), "cuda")
+    e2e_val = e2e_pairs / e2e_t
 
     # dominant kernel: per-kernel CUDA-event durations on the launching stream
     kt = sim.time_kernels(200)
