@@ -32,7 +32,7 @@ typedef struct lpv_config {
     int32_t na;                  /* ARX order of the least-squares start; n_x = na * n_y */
     int32_t adam_iters;          /* Adam iterations per restart (Section 5.3.2: 2000)    */
     int32_t restarts;            /* random restarts, best training loss kept (paper: 8)  */
-    int32_t reserved;
+    int32_t lbfgs_iters;         /* L-BFGS iterations after Adam, per restart (0: none)  */
     double lr, beta1, beta2, adam_eps;  /* Adam step size and moments                 */
     double sigma2;               /* l2 weight of the parameters, Eq. 27 (paper: 1e-4)   */
     double init_scale;           /* std of the normal draw of M_1..M_np per restart      */
@@ -122,10 +122,22 @@ int lpv_train(lpv_model* m, const float* u, const float* y, const float* p, int3
  * The identification of Section 5.3.2: lpv_normalize, lpv_init_ls, then for
  * each restart the B and C blocks of M_1..M_np drawn from N(0,
  * init_scale^2) (their A blocks start at 0, so the start keeps the stable
- * spectrum of M_0 for every p) and adam_iters Adam steps; keeps the restart with the lowest training loss.  best_loss (host)
+ * spectrum of M_0 for every p), adam_iters Adam steps and lbfgs_iters
+ * L-BFGS iterations; keeps the restart with the lowest training loss.  best_loss (host)
  * may be NULL.  Returns SPH_E_DIVERGED (and no model) when no restart ends
  * with a finite loss.  Blocks.
  */
+/*
+ * iters L-BFGS iterations (Section 5.3.2: after Adam): two-loop recursion over
+ * the last 10 curvature pairs in FP64 on the device, unit quasi-Newton step
+ * with Armijo backtracking (sufficient decrease 1e-4, halving); a pair is
+ * kept only when s.y > 0.  Stops early at a point where no decrease is found.
+ * loss_history (host [iters], may be NULL) records the accepted losses (the
+ * last one repeated after an early stop).  Resets the Adam state.  Blocks.
+ */
+int lpv_lbfgs(lpv_model* m, const float* u, const float* y, const float* p, int32_t n_traj, int32_t T, int32_t iters,
+              double* loss_history, void* stream);
+
 int lpv_fit(const float* u, const float* y, const float* p, int32_t n_traj, int32_t T, const lpv_config* cfg,
             lpv_model** out, double* best_loss, void* stream);
 

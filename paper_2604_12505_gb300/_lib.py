@@ -87,6 +87,7 @@ def _declare(L):
         "lpv_init_ls": ([vp, vp, vp, i32, i32, vp, vp], C.c_int),
         "lpv_loss_grad": ([vp, vp, vp, vp, i32, i32, dp, vp, vp], C.c_int),
         "lpv_train": ([vp, vp, vp, vp, i32, i32, i32, vp, vp], C.c_int),
+        "lpv_lbfgs": ([vp, vp, vp, vp, i32, i32, i32, vp, vp], C.c_int),
         "lpv_fit": ([vp, vp, vp, i32, i32, vp, C.POINTER(vp), dp, vp], C.c_int),
         "lpv_predict": ([vp, vp, vp, i32, i32, vp, vp], C.c_int),
         "lpv_simulate": ([vp, i32, vp, vp, vp, vp, i32, vp, vp, vp], C.c_int),

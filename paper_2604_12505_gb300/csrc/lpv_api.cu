@@ -32,6 +32,8 @@ struct lpv_model {
     int* status = nullptr;
     float *Wb = nullptr, *mb = nullptr, *vb = nullptr, *lr_scale = nullptr;  // last accepted Adam iterate
     double* acc_loss = nullptr;                                              // and its loss
+    double* lb = nullptr;  // L-BFGS state (allocated on first use)
+    int* lb_count = nullptr;
     int adam_t = 0;
 };
 
@@ -157,7 +159,8 @@ int lpv_destroy(lpv_model* M)
     for (void* p : {(void*)M->Wp, (void*)M->m, (void*)M->v, (void*)M->grad, (void*)M->hist, (void*)M->gpart,
                     (void*)M->loss_part, (void*)M->d_loss, (void*)M->d_hist, (void*)M->stats_part, (void*)M->stats,
                     (void*)M->gram_part, (void*)M->theta, (void*)M->rho, (void*)M->status, (void*)M->Wb,
-                    (void*)M->mb, (void*)M->vb, (void*)M->lr_scale, (void*)M->acc_loss})
+                    (void*)M->mb, (void*)M->vb, (void*)M->lr_scale, (void*)M->acc_loss, (void*)M->lb,
+                    (void*)M->lb_count})
         cudaFree(p);
     delete M;
     return SPH_OK;
@@ -336,6 +339,75 @@ int lpv_train(lpv_model* M, const float* u, const float* y, const float* p, int3
     return SPH_OK;
 }
 
+int lpv_lbfgs(lpv_model* M, const float* u, const float* y, const float* p, int32_t n_traj, int32_t T, int32_t iters,
+              double* loss_history, void* stream)
+{
+    int rc = check_data(M, u, y, p, n_traj, T);
+    if (rc) return rc;
+    if (iters < 0) return err(SPH_E_INVAL, "lpv_lbfgs: negative iteration count");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!M->lb) {
+        const size_t n = (size_t)kWN * (3 + 2 * kLbfgsM) + kLbfgsM + 2;
+        if (cudaMalloc(&M->lb, n * sizeof(double)) != cudaSuccess || cudaMalloc(&M->lb_count, 2 * sizeof(int)) != cudaSuccess)
+            return err(SPH_E_NOMEM, "lpv_lbfgs: cudaMalloc failed");
+    }
+    LbfgsDev L;
+    L.W = M->lb;
+    L.g = L.W + kWN;
+    L.d = L.g + kWN;
+    L.S = L.d + kWN;
+    L.Y = L.S + (size_t)kLbfgsM * kWN;
+    L.rho = L.Y + (size_t)kLbfgsM * kWN;
+    L.gd = L.rho + kLbfgsM;
+    L.count = M->lb_count;
+    auto loss_now = [&](double* out) -> int {
+        int r = loss_grad_device(M, u, y, p, n_traj, T, nullptr, 0, st);
+        if (r) return r;
+        LCK(cudaMemcpyAsync(out, M->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        LCK(cudaStreamSynchronize(st));
+        return SPH_OK;
+    };
+    double f = 0.0;
+    if ((rc = loss_now(&f))) return rc;
+    if (!std::isfinite(f)) return err(SPH_E_DIVERGED, "lpv_lbfgs: the loss at the start is not finite");
+    LCK(launch_lbfgs_init(M->Wp, M->grad, M->d, L, st));
+    constexpr double kArmijo = 1e-4;
+    int it = 0;
+    for (; it < iters; ++it) {
+        LCK(launch_lbfgs_dir(L, st));
+        double gd[2];
+        int cnt[2];
+        LCK(cudaMemcpyAsync(gd, L.gd, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LCK(cudaMemcpyAsync(cnt, L.count, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        LCK(cudaStreamSynchronize(st));
+        if (!(gd[0] < 0.0)) break;  // stationary point
+        // unit quasi-Newton step; after a reset, a step of 0.01 in the weights
+        double step = cnt[0] > 0 ? 1.0 : std::min(1.0, 0.01 / std::sqrt(gd[1]));
+        bool ok = false;
+        double fn = 0.0;
+        for (int tries = 0; tries < 40; ++tries) {
+            LCK(launch_lbfgs_try(M->Wp, M->d, L, step, st));
+            if ((rc = loss_now(&fn))) return rc;
+            if (std::isfinite(fn) && fn <= f + kArmijo * step * gd[0]) {
+                ok = true;
+                break;
+            }
+            step *= 0.5;
+        }
+        if (!ok) {  // no decrease along d: keep the last accepted point
+            LCK(launch_lbfgs_try(M->Wp, M->d, L, 0.0, st));
+            break;
+        }
+        LCK(launch_lbfgs_accept(M->grad, M->d, L, step, st));
+        f = fn;
+        if (loss_history) loss_history[it] = f;
+    }
+    if (loss_history)
+        for (int k = it; k < iters; ++k) loss_history[k] = f;
+    LCK(cudaStreamSynchronize(st));
+    return reset_optimizer(M);
+}
+
 int lpv_fit(const float* u, const float* y, const float* p, int32_t n_traj, int32_t T, const lpv_config* cfg,
             lpv_model** out, double* best_loss, void* stream)
 {
@@ -369,6 +441,11 @@ int lpv_fit(const float* u, const float* y, const float* p, int32_t n_traj, int3
         }
         if ((rc = lpv_set_params(M, W.data(), nullptr))) return bail(rc);
         if ((rc = lpv_train(M, u, y, p, n_traj, T, cfg->adam_iters, nullptr, stream))) return bail(rc);
+        if (cfg->lbfgs_iters > 0) {
+            rc = lpv_lbfgs(M, u, y, p, n_traj, T, cfg->lbfgs_iters, nullptr, stream);
+            if (rc == SPH_E_DIVERGED) continue;  // this restart ended with a non-finite loss
+            if (rc) return bail(rc);
+        }
         double L = 0.0;
         if ((rc = lpv_loss_grad(M, u, y, p, n_traj, T, &L, nullptr, stream))) return bail(rc);
         if (L < best) {

@@ -47,4 +47,17 @@ cudaError_t launch_gram(const float* u, const float* y, int n_traj, int T, const
 cudaError_t launch_ls_solve(const double* part, const Dims& d, int na, double rho_max, double* theta, float* Wp,
                             int* status, double* rho_out, cudaStream_t st);
 
+// L-BFGS state (device): FP64 master weights, gradient, search direction,
+// kLbfgsM curvature pairs (S, Y, rho), count[0] = stored pairs, count[1] =
+// next slot, gd[0] = g.d, gd[1] = g.g.
+constexpr int kLbfgsM = 10;
+struct LbfgsDev {
+    double *W, *g, *d, *S, *Y, *rho, *gd;
+    int* count;
+};
+cudaError_t launch_lbfgs_init(const float* Wp, const float* grad, const Dims& d, const LbfgsDev& L, cudaStream_t st);
+cudaError_t launch_lbfgs_dir(const LbfgsDev& L, cudaStream_t st);
+cudaError_t launch_lbfgs_try(float* Wp, const Dims& d, const LbfgsDev& L, double step, cudaStream_t st);
+cudaError_t launch_lbfgs_accept(const float* grad, const Dims& d, const LbfgsDev& L, double step, cudaStream_t st);
+
 }  // namespace lpv

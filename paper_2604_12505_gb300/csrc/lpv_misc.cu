@@ -572,3 +572,143 @@ cudaError_t launch_ls_solve(const double* part, const Dims& d, int na, double rh
 }
 
 }  // namespace lpv
+
+namespace lpv {
+
+// ---------------------------------------------------------------------------
+// L-BFGS (Nocedal and Wright, Algorithm 7.4) on the trainable weights: FP64
+// master weights, gradient and curvature pairs; one block of kWN threads
+// (one per padded weight), fixed-order FP64 block reductions.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ double block_dot(double v, double* red)
+{
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) v += __shfl_down_sync(0xffffffffu, v, s);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kWN / 32; ++w) t += red[w];
+    return t;  // every thread
+}
+
+}  // namespace
+
+__global__ void lbfgs_init_kernel(const float* __restrict__ Wp, const float* __restrict__ grad, Dims d, LbfgsDev L)
+{
+    const int i = threadIdx.x;
+    const bool tr = trainable(d, i / (kFB * kMaxKT), i % (kFB * kMaxKT));
+    L.W[i] = tr ? (double)Wp[i] : 0.0;
+    L.g[i] = tr ? (double)grad[i] : 0.0;
+    if (i == 0) {
+        L.count[0] = 0;
+        L.count[1] = 0;
+    }
+}
+
+// d = -H g by the two-loop recursion over the stored pairs (newest first),
+// H_0 = (s.y / y.y) I of the newest pair; falls back to d = -g (and clears the
+// history) when that is not a descent direction.  Writes g.d and g.g.
+__global__ void lbfgs_dir_kernel(LbfgsDev L)
+{
+    __shared__ double red[kWN / 32];
+    __shared__ double alpha[kLbfgsM];
+    const int i = threadIdx.x;
+    const int n = L.count[0], next = L.count[1];
+    double q = L.g[i];
+    for (int k = 0; k < n; ++k) {
+        const int j = (next - 1 - k + kLbfgsM) % kLbfgsM;
+        const double a = L.rho[j] * block_dot(L.S[j * kWN + i] * q, red);
+        if (i == 0) alpha[j] = a;
+        q -= a * L.Y[j * kWN + i];
+    }
+    double gamma = 1.0;
+    if (n > 0) {
+        const int j = (next - 1 + kLbfgsM) % kLbfgsM;
+        const double yy = block_dot(L.Y[j * kWN + i] * L.Y[j * kWN + i], red);
+        gamma = yy > 0.0 ? 1.0 / (L.rho[j] * yy) : 1.0;
+    }
+    __syncthreads();
+    double r = gamma * q;
+    for (int k = n - 1; k >= 0; --k) {
+        const int j = (next - 1 - k + kLbfgsM) % kLbfgsM;
+        const double b = L.rho[j] * block_dot(L.Y[j * kWN + i] * r, red);
+        r += L.S[j * kWN + i] * (alpha[j] - b);
+    }
+    const double gi = L.g[i];
+    const double gd = -block_dot(gi * r, red);
+    const double gg = block_dot(gi * gi, red);
+    if (gd < 0.0) {
+        L.d[i] = -r;
+        if (i == 0) L.gd[0] = gd;
+    } else {
+        L.d[i] = -gi;
+        if (i == 0) {
+            L.gd[0] = -gg;
+            L.count[0] = 0;
+        }
+    }
+    if (i == 0) L.gd[1] = gg;
+}
+
+// Wp = W + step d on the trainable entries (the trial point).
+__global__ void lbfgs_try_kernel(float* __restrict__ Wp, Dims d, LbfgsDev L, double step)
+{
+    const int i = threadIdx.x;
+    const bool tr = trainable(d, i / (kFB * kMaxKT), i % (kFB * kMaxKT));
+    Wp[i] = tr ? (float)(L.W[i] + step * L.d[i]) : 0.f;
+}
+
+// Accepts the trial point: s = step d, y = g_new - g; the pair is stored when
+// s.y > 0 (curvature condition), then W and g move to the new point.
+__global__ void lbfgs_accept_kernel(const float* __restrict__ grad, Dims d, LbfgsDev L, double step)
+{
+    __shared__ double red[kWN / 32];
+    const int i = threadIdx.x;
+    const bool tr = trainable(d, i / (kFB * kMaxKT), i % (kFB * kMaxKT));
+    const double gn = tr ? (double)grad[i] : 0.0;
+    const double s = step * L.d[i], y = gn - L.g[i];
+    const double sy = block_dot(s * y, red);
+    const double yy = block_dot(y * y, red);
+    const int next = L.count[1];
+    __syncthreads();
+    if (sy > 1e-12 * yy && sy > 0.0) {
+        L.S[next * kWN + i] = s;
+        L.Y[next * kWN + i] = y;
+        if (i == 0) {
+            L.rho[next] = 1.0 / sy;
+            L.count[0] = min(L.count[0] + 1, kLbfgsM);
+            L.count[1] = (next + 1) % kLbfgsM;
+        }
+    }
+    L.W[i] += s;
+    L.g[i] = gn;
+}
+
+cudaError_t launch_lbfgs_init(const float* Wp, const float* grad, const Dims& d, const LbfgsDev& L, cudaStream_t st)
+{
+    lbfgs_init_kernel<<<1, kWN, 0, st>>>(Wp, grad, d, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs_dir(const LbfgsDev& L, cudaStream_t st)
+{
+    lbfgs_dir_kernel<<<1, kWN, 0, st>>>(L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs_try(float* Wp, const Dims& d, const LbfgsDev& L, double step, cudaStream_t st)
+{
+    lbfgs_try_kernel<<<1, kWN, 0, st>>>(Wp, d, L, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_lbfgs_accept(const float* grad, const Dims& d, const LbfgsDev& L, double step, cudaStream_t st)
+{
+    lbfgs_accept_kernel<<<1, kWN, 0, st>>>(grad, d, L, step);
+    return cudaGetLastError();
+}
+
+}  // namespace lpv

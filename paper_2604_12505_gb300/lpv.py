@@ -16,7 +16,7 @@ class LpvConfig(C.Structure):
 
     _fields_ = [
         ("n_x", C.c_int32), ("n_u", C.c_int32), ("n_y", C.c_int32), ("n_p", C.c_int32), ("na", C.c_int32),
-        ("adam_iters", C.c_int32), ("restarts", C.c_int32), ("reserved", C.c_int32),
+        ("adam_iters", C.c_int32), ("restarts", C.c_int32), ("lbfgs_iters", C.c_int32),
         ("lr", C.c_double), ("beta1", C.c_double), ("beta2", C.c_double), ("adam_eps", C.c_double),
         ("sigma2", C.c_double), ("init_scale", C.c_double), ("seed", C.c_uint64), ("rho_max", C.c_double),
     ]
@@ -29,7 +29,7 @@ class LpvBody(C.Structure):
     ]
 
 
-DEFAULT = dict(n_x=12, n_u=3, n_y=4, n_p=2, na=3, adam_iters=2000, restarts=8, lr=1e-3, beta1=0.9, beta2=0.999,
+DEFAULT = dict(n_x=12, n_u=3, n_y=4, n_p=2, na=3, adam_iters=2000, restarts=8, lbfgs_iters=0, lr=1e-3, beta1=0.9, beta2=0.999,
                adam_eps=1e-8, sigma2=1e-4, init_scale=1e-2, seed=7, rho_max=0.999)
 
 
@@ -116,6 +116,15 @@ class Model:
         hist = np.zeros(max(iters, 1))
         check(lib().lpv_train(self._h, _ptr(u), _ptr(y), _ptr(p), n, T, iters, hist.ctypes.data_as(C.c_void_p),
                               _stream(stream)), "lpv_train")
+        return hist[:iters]
+
+    def lbfgs(self, u, y, p, iters: int, stream=None):
+        """L-BFGS iterations from the current weights (lpv_lbfgs); returns the
+        accepted loss of each iteration."""
+        u, y, p, n, T = self._data(u, y, p)
+        hist = np.zeros(max(iters, 1))
+        check(lib().lpv_lbfgs(self._h, _ptr(u), _ptr(y), _ptr(p), n, T, iters, hist.ctypes.data_as(C.c_void_p),
+                              _stream(stream)), "lpv_lbfgs")
         return hist[:iters]
 
     def predict(self, u, p, stream=None):

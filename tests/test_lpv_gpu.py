@@ -253,3 +253,39 @@ def test_non_finite_steps_are_rejected_and_retried_smaller():
     assert np.isfinite(hist[-1])
     W, _ = m.get_params()
     assert np.all(np.isfinite(W))
+
+
+def test_lbfgs_descends_monotonically_and_outpaces_adam_near_a_teacher():
+    need_gpu()
+    rng = np.random.default_rng(7)
+    Wt = _stable_W(rng)
+    u, p = _data(rng, 64, 80)
+    y = np.stack([L.simulate(Wt, u[b], p[b], NX)[0] for b in range(64)])
+    mask = L.d_mask(NX, NU, NY, NP)
+    W0 = Wt + 0.02 * rng.normal(size=Wt.shape) * mask
+    runs = {}
+    for name in ("lbfgs", "adam"):
+        m = _model(sigma2=0.0, lr=1e-3)
+        m.set_params(W0.reshape(NX + NY, 1 + NP, NX + NU).transpose(1, 0, 2), _unit_scales())
+        l0, _ = m.loss_grad(u, y, p)
+        hist = m.lbfgs(u, y, p, 40) if name == "lbfgs" else m.train(u, y, p, 40)
+        runs[name] = (l0, hist, m.get_params()[0])
+    l0, h, Wl = runs["lbfgs"]
+    assert np.all(np.diff(h) <= 0.0), h          # Armijo: accepted losses never increase
+    assert h[-1] < 1e-2 * l0, (l0, h[-1])
+    assert h[-1] < 0.25 * runs["adam"][1][-1], (h[-1], runs["adam"][1][-1])
+    Wl = Wl.transpose(1, 0, 2).reshape(NX + NY, -1)
+    assert np.all(Wl[mask == 0] == 0.0)
+
+
+def test_fit_with_lbfgs_ends_no_worse_than_adam_alone():
+    need_gpu()
+    from paper_2604_12505_gb300 import lpv
+    rng = np.random.default_rng(8)
+    Wt = _stable_W(rng)
+    u, p = _data(rng, 48, 60)
+    y = np.stack([L.simulate(Wt, u[b], p[b], NX)[0] for b in range(48)])
+    cfg = dict(adam_iters=100, restarts=2, lr=3e-3, sigma2=1e-6)
+    _, best_adam = lpv.fit(u, y, p, cfg)
+    _, best_both = lpv.fit(u, y, p, dict(cfg, lbfgs_iters=50))
+    assert np.isfinite(best_both) and best_both <= best_adam
