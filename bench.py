@@ -214,7 +214,7 @@ SURROGATE_SIZES = {
     # 256 tanks x 4 launches = 1024 trajectories of 1000 samples; 64 held-out
     # closed-loop manoeuvres of 5000 steps; 65,536 surrogate runs
     "full": dict(n_tanks=256, launches=4, steps=10_000, relax=5000, cl_tanks=64, cl_steps=5000, n_sims=65_536,
-                 fit_cfg=dict(adam_iters=2000, restarts=8, lbfgs_iters=500)),
+                 fit_cfg=dict(adam_iters=2000, restarts=8, lbfgs_iters=100)),
     "small": dict(n_tanks=32, launches=1, steps=10_000, relax=5000, cl_tanks=16, cl_steps=5000, n_sims=65_536,
                   fit_cfg=dict(adam_iters=300, restarts=2)),
 }
