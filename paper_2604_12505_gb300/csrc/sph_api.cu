@@ -261,6 +261,7 @@ TankDev make_tank_dev(const TankHost& t)
     for (int g = 0; g < t.n_g; ++g) rmin = std::min(rmin, std::hypot(t.gB[2 * g], t.gB[2 * g + 1]));
     const double rin = rmin - t.cell * 1.01;
     d.ghost_rin2 = rin > 0 ? (float)(rin * rin) : -1.0f;
+    d.clip = (float)(2.0 * t.h * (1.0 + 1e-3));
     d.G = t.G;
     d.n_f = t.n_f;
     d.n_g = t.n_g;

@@ -36,6 +36,7 @@ struct TankDev {
     float inv_cell;               // fl32(1/s)
     float g_orig, g_inv_cell;     // body-frame ghost grid origin (-W) and 1/s, FP32
     float ghost_rin2;             // particles with |xi|^2 below this see no ghost
+    float clip;                   // 2h (1 + 1e-3): a candidate whose x-separation exceeds it lies outside the support
     int G;                        // cells per side (fluid and ghost grid)
     int n_f, n_g;
     int cell_base;                // first cell of this tank in the global grid arrays

@@ -8,8 +8,9 @@
 //                   arithmetic on the FP32 pipe), Eqs. 14 and 11 (+ the
 //                   continuity sum): one CTA per tile of TX x TY grid cells;
 //                   the tile plus a one-cell halo is staged in shared memory,
-//                   ordered by particle index inside each cell, and every own
-//                   particle sums over its 3x3 cells.
+//                   each cell ordered by x (then particle index), and every own
+//                   particle sums over its 3x3 cells, each row clipped in x to
+//                   the part that can lie within the support.
 //   force_kernel    Eqs. 10, 12 (fluid pairs), 16-19 (ghost pairs), the fluid
 //                   acceleration of Algorithm 1, kick-then-drift of the fluid,
 //                   and the re-binning of the moved particle into the other
@@ -81,9 +82,16 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
         const bool rec = t < Sh::MAXOWN;
         unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
         int nn = 0;
+        const float xlo = pi.x - T.clip, xhi = pi.x + T.clip;
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
-            const int a = sm.start[c + dy * Sh::SX - 1], z = sm.start[c + dy * Sh::SX + 2];
+            // each cell is sorted by x: of the row's left cell only the suffix
+            // with x >= x_i - clip, of its right cell only the prefix with
+            // x < x_i + clip can lie within the support (clip = 2h (1 + 1e-3)
+            // keeps every FP32 decision r^2 < (2h)^2 inside the range)
+            const int cl = c + dy * Sh::SX - 1;
+            const int a = lower_x(sm, sm.start[cl], sm.start[cl + 1], xlo);
+            const int z = lower_x(sm, sm.start[cl + 2], sm.start[cl + 3], xhi);
             for (int j = a; j < z; ++j) {
                 const float4 pj = sm.pv[j];
                 const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);

@@ -32,6 +32,7 @@ struct Stage {
     float4 pv[Sh::MAXS];
     int pid[Sh::MAXS];
     int pid_in[Sh::MAXS];         // particle index in global slot order (before ordering)
+    unsigned int key_in[Sh::MAXS];  // ordering key of x in global slot order
     int slot[Sh::MAXS];
     unsigned char cell[Sh::MAXS];
     float2 rho[RHO ? Sh::MAXS : 1];
@@ -39,9 +40,20 @@ struct Stage {
     float2 trho[(TAN && RHO) ? Sh::MAXS : 1];  // tangent (d rho, d(P / rho^2))
 };
 
+// Key with the IEEE-754 total order of x (NaNs included, -0 below +0): with
+// the particle index as a tie-break the ranks inside a cell always form a
+// permutation, whatever the values.
+__device__ __forceinline__ unsigned int order_key(float x)
+{
+    const unsigned int u = __float_as_uint(x);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
 // Loads the counts, scans them, and gathers the particles of the (TX+2) x
-// (TY+2) staged cells, each cell ordered by particle index.  Returns false
-// (uniformly over the block) if the staged set does not fit.
+// (TY+2) staged cells, each cell ordered by x with the particle index
+// breaking ties (a deterministic order, whatever order the slots were
+// claimed in).  Returns false (uniformly over the block) if the staged set
+// does not fit.
 template <int TX, int TY, bool RHO, bool TAN>
 __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, int cy0, Stage<TX, TY, RHO, TAN>& sm)
 {
@@ -96,18 +108,25 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
         }
         const int ix = cx0 - 1 + lo % Sh::SX, iy = cy0 - 1 + lo / Sh::SX;
         sm.cell[e] = (unsigned char)lo;
-        sm.pid_in[e] = S.pid[buf][(T.cell_base + iy * T.G + ix) * kCap + (e - sm.start[lo])];
+        const int gs = (T.cell_base + iy * T.G + ix) * kCap + (e - sm.start[lo]);
+        sm.pid_in[e] = S.pid[buf][gs];
+        sm.key_in[e] = order_key(S.pv[buf][gs].x);
     }
     __syncthreads();
-    // pass 2: rank by particle index inside the cell and gather into that
-    // order (reads only cell[], pid_in[] and start[], which pass 2 never writes)
+    // pass 2: rank by (x, particle index) inside the cell and gather into
+    // that order (reads only cell[], pid_in[], x_in[] and start[], which pass 2
+    // never writes)
 #pragma unroll 2
     for (int e = tid; e < total; e += blockDim.x) {
         const int c = sm.cell[e];
         const int a = sm.start[c];
         const int id = sm.pid_in[e];
+        const unsigned int ke = sm.key_in[e];
         int rank = 0;
-        for (int j = a; j < sm.start[c + 1]; ++j) rank += (sm.pid_in[j] < id);
+        for (int j = a; j < sm.start[c + 1]; ++j) {
+            const unsigned int kj = sm.key_in[j];
+            rank += (kj < ke) || (kj == ke && sm.pid_in[j] < id);
+        }
         const int d = a + rank;
         const int ix = cx0 - 1 + c % Sh::SX, iy = cy0 - 1 + c / Sh::SX;
         const int gs = (T.cell_base + iy * T.G + ix) * kCap + (e - a);
@@ -122,6 +141,18 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
     }
     __syncthreads();
     return true;
+}
+
+// First staged index in [lo, hi) whose x is not below v (a cell is sorted by
+// x; with a NaN present the answer is only some index in [lo, hi]).
+template <class Stg>
+__device__ __forceinline__ int lower_x(const Stg& sm, int lo, int hi, float v)
+{
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (sm.pv[mid].x < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
 }
 
 // Smem index of the t-th own particle (own cells are TY contiguous row runs).
