@@ -150,10 +150,11 @@ def algorithmic_flop_force(n_ff, n_fg, n_f):
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock.
 FP32_LANES = 152 * 128
 
-# DRAM bytes (read + write) per launch of force_kernel<8, 4> on the large tank,
-# mean of three launches captured warm (ncu --cache-control none): the working
-# set stays in L2.  Valid for the kernel source it was captured on.
-FORCE_84_TRAFFIC_BYTES = 20_736
+# DRAM bytes (read + write) per launch of force_kernel on the large tank, by
+# tile code, mean of three launches captured warm (ncu --cache-control none):
+# the working set stays in L2.  Valid for the kernel source they were
+# captured on; a tile without a capture reports null.
+FORCE_TRAFFIC_BYTES = {3: 27_221, 4: 21_589}
 
 
 # --------------------------------------------------------------------------
@@ -372,7 +373,7 @@ def run_ours(a):
     # above this GPU's FP32 ridge and its data stay in L2: FP32-ALU roofline
     roof = {"bound": "alu", "kernel": "force_kernel", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": tflops / fp32_peak,
-            "traffic": FORCE_84_TRAFFIC_BYTES if tile == 4 else None,
+            "traffic": FORCE_TRAFFIC_BYTES.get(tile),
             "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
             "algorithmic_flop": flop, "intensity_flop_per_byte": flop / ab["force"],
             "kernel_us": kt, "dominant": f"{dom}_kernel",
