@@ -214,6 +214,7 @@ void free_sim(sph_sim* s)
     cudaFree(s->S.gpartials);
     cudaFree(s->S.nbl);
     cudaFree(s->S.nbn);
+    cudaFree(s->S.srec);
     for (int b = 0; b < 2; ++b) cudaFree(s->S.tpv[b]);
     cudaFree(s->S.trho);
     cudaFree(s->S.tgh);
@@ -262,6 +263,8 @@ TankDev make_tank_dev(const TankHost& t)
     const double rin = rmin - t.cell * 1.01;
     d.ghost_rin2 = rin > 0 ? (float)(rin * rin) : -1.0f;
     d.clip = (float)(2.0 * t.h * (1.0 + 1e-3));
+    d.hclip = (float)(t.h * (1.0 + 1e-3));
+    d.g_cell = (float)t.cell;
     d.G = t.G;
     d.n_f = t.n_f;
     d.n_g = t.n_g;
@@ -306,6 +309,8 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
         td[b].pid_base = pid_base;
         // ghosts sorted by body-frame cell (stable), cell table with global indices
         const int G = t.G;
+        // within a cell by body-frame x (then index), so that a row of cells is
+        // sorted by x and the kernels can clip it to the support's x-range
         std::vector<int> key(t.n_g), order(t.n_g);
         for (int g = 0; g < t.n_g; ++g) {
             int cx = (int)std::floor((t.gB[2 * g] + t.W) / t.cell), cy = (int)std::floor((t.gB[2 * g + 1] + t.W) / t.cell);
@@ -314,7 +319,10 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
             key[g] = cy * G + cx;
             order[g] = g;
         }
-        std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return key[a] < key[c]; });
+        std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+            if (key[a] != key[c]) return key[a] < key[c];
+            return t.gB[2 * a] < t.gB[2 * c];
+        });
         std::vector<int> cnt((size_t)G * G + 1, 0);
         for (int g = 0; g < t.n_g; ++g) cnt[key[g] + 1]++;
         for (size_t c = 0; c < (size_t)G * G; ++c) cnt[c + 1] += cnt[c];
@@ -405,6 +413,7 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
         rc |= dalloc(&s->S.nbn, nn);
     }
     rc |= dalloc(&s->S.gdone, max_groups);
+    rc |= dalloc(&s->S.srec, stage_record_bytes(s->n_tiles));
     float4* gB_d;
     int* gstart_d;
     rc |= dalloc(&gB_d, gB_sorted.size());

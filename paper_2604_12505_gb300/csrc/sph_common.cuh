@@ -7,8 +7,8 @@
 //     particle's global index.  The fluid state lives only in these slots:
 //     the force kernel integrates a particle and writes it straight into its
 //     cell of the other buffer (atomic slot claim), so no sort or scan pass
-//     exists.  Within a cell the kernels order particles by index, which
-//     makes every neighbour sum deterministic.
+//     exists.  Within a cell the kernels order particles by x, then by
+//     index, which makes every neighbour sum deterministic.
 //   * per-slot float2 (rho, P / rho^2) written by the density kernel.
 //   * ghosts: body-frame positions (two-float) binned once into a body-frame
 //     grid, and per step the world position as an FP32 (hi, lo) pair plus
@@ -37,6 +37,8 @@ struct TankDev {
     float g_orig, g_inv_cell;     // body-frame ghost grid origin (-W) and 1/s, FP32
     float ghost_rin2;             // particles with |xi|^2 below this see no ghost
     float clip;                   // 2h (1 + 1e-3): a candidate whose x-separation exceeds it lies outside the support
+    float hclip;                  // h (1 + 1e-3): likewise for the ghost terms of the force pass (support h)
+    float g_cell;                 // fl32(ghost-grid cell side)
     int G;                        // cells per side (fluid and ghost grid)
     int n_f, n_g;
     int cell_base;                // first cell of this tank in the global grid arrays
@@ -177,6 +179,7 @@ struct SimDev {
     float4* gvel;                 // per step: (v_x, v_y, arm_x, arm_y)
     unsigned short* nbl;          // per tile [kNbrMax][max own]: staged index of each fluid neighbour
     unsigned char* nbn;           // per tile [max own]: neighbour count (> kNbrMax: not recorded)
+    unsigned char* srec;          // per tile: the staged order the density pass leaves for the force pass (StageRec)
     // forward-mode tangent (JVP) state, allocated on first use
     float4* tpv[2];               // per slot (dx, dy, dvx, dvy), binned with the primal
     float2* trho;                 // per slot (d rho, d(P / rho^2))

@@ -20,6 +20,7 @@
 //                   (Eq. 20), samples outputs and runs the PD law (Eq. 28).
 // No warp-wide FP64 arithmetic runs in the tile kernels: this GPU's FP64
 // pipe issues a warp instruction in about 16 cycles per SM.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -35,10 +36,12 @@ namespace sph {
 // TAN: also the forward-mode tangent d rho (Eq. 14 differentiated along the
 // tangent of positions and of the body pose) and d(P / rho^2).
 template <int TX, int TY, bool TAN>
-__global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev S, EvalOut E, int eval)
+__global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY>::DENSITY_MIN_CTAS)
+    density_kernel(SimDev S, EvalOut E, int eval)
 {
     using Sh = Shape<TX, TY>;
     __shared__ Stage<TX, TY, false, TAN> sm;
+    __shared__ GhostStage<!TAN> gs;
     pdl_trigger();
     const int4 td = S.tiles[blockIdx.x];
     const TankDev T = S.tank[td.x];  // by value: the constants live in registers
@@ -51,14 +54,18 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
         int ix = cx0 + c % TX, iy = cy0 + c / TX;
         if (ix < T.G && iy < T.G) S.count[nbuf][T.cell_base + iy * T.G + ix] = 0;
     }
-    if (!stage_tile<TX, TY, false, TAN>(S, T, buf, cx0, cy0, sm)) return;
+    const bool staged = stage_tile<TX, TY, false, TAN>(S, T, buf, cx0, cy0, sm);
+    save_stage(sm, staged, stage_record<TX, TY>(S, blockIdx.x));
+    if (!staged) return;
     const int n_own = sm.own_row[TY];
     if (n_own == 0) return;
 
     const BodyDev& b = S.body[td.x];
+    int gmode = kGhostsGlobal;  // the tangent variant visits the ghosts through global memory
+    if constexpr (!TAN) gmode = stage_ghosts<true>(S, T, b, sm, n_own, gs);
     const float bc = b.fc, bs = b.fs, brx = b.frx, bry = b.fry;
-    const float2 dc = b.dc, ds = b.ds, drx = b.drx, dry = b.dry;
-    const float fvx = b.fvx, fvy = b.fvy, fw = b.fw;
+    const GhostFrame fr = ghost_frame(b);
+    const float fw = fr.fw;
     const bool want_drho = eval && E.drho;
     float t_rx = 0.f, t_ry = 0.f, t_th = 0.f, t_vx = 0.f, t_vy = 0.f, t_w = 0.f;
     if constexpr (TAN) {
@@ -118,28 +125,11 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
         if (rec) S.nbn[blockIdx.x * Sh::MAXOWN + t] = (unsigned char)min(nn, 255);
         float Sg = 0.f, Dg = 0.f;
         int ng2 = 0;
-        for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
-            // Eq. 21 in two-float arithmetic: arm = R(theta) r_g^B, r_g = r + arm,
-            // v_g = rdot + thetadot z x arm; stored for the force pass
-            const float4 gb = __ldg(S.gB + g);
-            const float2 bx = make_float2(gb.x, gb.y), by = make_float2(gb.z, gb.w);
-            const float2 sby = df_mul(ds, by);
-            const float2 ax = df_add(df_mul(dc, bx), make_float2(-sby.x, -sby.y));
-            const float2 ay = df_add(df_mul(ds, bx), df_mul(dc, by));
-            const float2 gx = df_add(drx, ax), gy = df_add(dry, ay);
-            const float armx = ax.x + ax.y, army = ay.x + ay.y;
-            const float vgx = fvx - fw * army, vgy = fvy + fw * armx;
-            S.gpos[g] = make_float4(gx.x, gy.x, gx.y, gy.y);
-            S.gvel[g] = make_float4(vgx, vgy, armx, army);
-            float tgx = 0.f, tgy = 0.f;
-            if constexpr (TAN) {  // d r_g = d r + d theta z x arm, d v_g likewise (Eq. 21)
-                tgx = t_rx - t_th * army;
-                tgy = t_ry + t_th * armx;
-                S.tgh[g] = make_float4(tgx, tgy, t_vx - t_w * army - fw * t_th * armx,
-                                       t_vy + t_w * armx - fw * t_th * army);
-            }
-            const float ddx = __fsub_rn(__fsub_rn(pi.x, gx.x), gx.y);
-            const float ddy = __fsub_rn(__fsub_rn(pi.y, gy.x), gy.y);
+        // one ghost within reach: gp = (x_hi, y_hi, x_lo, y_lo) world position,
+        // gv = (v_x, v_y, arm_x, arm_y) (Eq. 21), (tgx, tgy) its position tangent
+        auto ghost = [&](const float4 gp, const float4 gv, float tgx, float tgy) {
+            const float ddx = __fsub_rn(__fsub_rn(pi.x, gp.x), gp.z);
+            const float ddy = __fsub_rn(__fsub_rn(pi.y, gp.y), gp.w);
             const float r2 = dist2(ddx, ddy);
             if (r2 < T.R2) {
                 ++ng2;
@@ -147,12 +137,34 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) density_kernel(SimDev 
                 const float r = r2 * inv_r;
                 Sg += (r2 > 0.f) ? w_cubic(T, r) : T.cW * 4.0f;
                 if (want_drho && r2 > 0.f)
-                    Dg += ((pi.z - vgx) * ddx + (pi.w - vgy) * ddy) * dw_cubic_over_r(T, r, inv_r);
+                    Dg += ((pi.z - gv.x) * ddx + (pi.w - gv.y) * ddy) * dw_cubic_over_r(T, r, inv_r);
                 if constexpr (TAN) {
                     if (r2 > 0.f) dRg += (ddx * (ti.x - tgx) + ddy * (ti.y - tgy)) * dw_cubic_over_r(T, r, inv_r);
                 }
             }
-        });
+        };
+        if (gmode == kGhostsStaged) {
+            if constexpr (!TAN)
+                for_staged_ghosts(T, gs, pi.x, pi.y, bc, bs, brx, bry, T.clip,
+                                  [&](int, int sg) { ghost(gs.gp[sg], gs.gv[sg], 0.f, 0.f); });
+        } else if (gmode == kGhostsGlobal) {
+            // Eq. 21 per visit, stored for the force pass and the adjoint
+            for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
+                float4 gp, gv;
+                ghost_world(fr, __ldg(S.gB + g), gp, gv);
+                S.gpos[g] = gp;
+                S.gvel[g] = gv;
+                float tgx = 0.f, tgy = 0.f;
+                if constexpr (TAN) {  // d r_g = d r + d theta z x arm, d v_g likewise (Eq. 21)
+                    const float armx = gv.z, army = gv.w;
+                    tgx = t_rx - t_th * army;
+                    tgy = t_ry + t_th * armx;
+                    S.tgh[g] = make_float4(tgx, tgy, t_vx - t_w * army - fw * t_th * armx,
+                                           t_vy + t_w * armx - fw * t_th * army);
+                }
+                ghost(gp, gv, tgx, tgy);
+            });
+        }
         const float rho = T.m * (Sf + T.gamma1 * Sg);          // Eq. 14
         const float P = T.k * (rho - T.rho0);                  // Eq. 11
         const float pr2 = P / (rho * rho);
@@ -399,10 +411,12 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
 // TAN: also the forward-mode tangent of the accelerations, of the step and of
 // the body force/torque, along the tangent staged with the particles.
 template <int TX, int TY, bool TAN>
-__global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S, EvalOut E, int eval)
+__global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY>::FORCE_MIN_CTAS)
+    force_kernel(SimDev S, EvalOut E, int eval)
 {
     using Sh = Shape<TX, TY>;
     __shared__ Stage<TX, TY, true, TAN> sm;
+    __shared__ GhostStage<!TAN> gs;
     __shared__ Red scratch[32];
     __shared__ int is_last;
     pdl_trigger();
@@ -420,11 +434,13 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
     Red acc{z, z, z, z, z, 0ull};
     Red tacc{z, z, z, z, z, 0ull};
     int flags = 0, wall = 0;
-    if (stage_tile<TX, TY, true, TAN>(S, T, buf, cx0, cy0, sm)) {
+    if (stage_from_record<TX, TY, TAN>(S, tank, buf, stage_record<TX, TY>(S, blockIdx.x), sm)) {
         const BodyDev& b = S.body[tank];
+        const int n_own = sm.own_row[TY];
+        int gmode = kGhostsGlobal;  // the tangent variant visits the ghosts through global memory
+        if constexpr (!TAN) gmode = n_own > 0 ? stage_ghosts<false>(S, T, b, sm, n_own, gs) : kGhostsNone;
         const float bc = b.fc, bs = b.fs, brx = b.frx, bry = b.fry;
         const float ox = b.fo_next[0], oy = b.fo_next[1];  // origin of the next grid
-        const int n_own = sm.own_row[TY];
         const float mm = T.m * T.m;
         float wfx = 0.f, wfy = 0.f, wt = 0.f, cxs = 0.f, cys = 0.f;
         float twfx = 0.f, twfy = 0.f, twt = 0.f, tcxs = 0.f, tcys = 0.f;
@@ -495,15 +511,16 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
                 }
             }
             int nfg = 0;
-            for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
-                const float4 gp = __ldg(S.gpos + g);
+            // one ghost: gp its world position (x_hi, y_hi, x_lo, y_lo), load_gv()
+            // its (v_x, v_y, arm_x, arm_y), read only for a pair within reach
+            auto ghost = [&](int g, const float4 gp, auto&& load_gv) {
                 const float ddx = __fsub_rn(__fsub_rn(pi.x, gp.x), gp.z);
                 const float ddy = __fsub_rn(__fsub_rn(pi.y, gp.y), gp.w);
                 const float r2 = dist2(ddx, ddy);
                 if (r2 < T.h2) {
                     ++nfg;
                     if (r2 > 0.f) {
-                        const float4 gv = __ldg(S.gvel + g);
+                        const float4 gv = load_gv();
                         const float inv_r = rsqrtf(r2);
                         const float r = r2 * inv_r;
                         const float d = T.h - r;
@@ -545,7 +562,15 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) force_kernel(SimDev S,
                         }
                     }
                 }
-            });
+            };
+            if (gmode == kGhostsStaged) {
+                if constexpr (!TAN)
+                    for_staged_ghosts(T, gs, pi.x, pi.y, bc, bs, brx, bry, T.hclip,
+                                      [&](int g, int sg) { ghost(g, gs.gp[sg], [&] { return gs.gv[sg]; }); });
+            } else if (gmode == kGhostsGlobal) {
+                for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry,
+                           [&](int g) { ghost(g, __ldg(S.gpos + g), [&] { return __ldg(S.gvel + g); }); });
+            }
             wall |= (nfg > 0);
             acc.pairs += (unsigned long long)(nff + nfg);
             cxs += pi.x;
@@ -826,6 +851,21 @@ static cudaError_t launch_tile_phase(const SimDev& S, const EvalOut& E, int eval
     }
     if (phase == 0) return launch(density_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
     return launch(force_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+}
+
+template <int TX, int TY>
+static size_t record_bytes(int n_tiles)
+{
+    return (size_t)n_tiles * sizeof(StageRec<TX, TY>);
+}
+
+size_t stage_record_bytes(const int* n_tiles)
+{
+    size_t b = record_bytes<2, 2>(n_tiles[1]);
+    b = std::max(b, record_bytes<4, 2>(n_tiles[2]));
+    b = std::max(b, record_bytes<4, 4>(n_tiles[3]));
+    b = std::max(b, record_bytes<8, 4>(n_tiles[4]));
+    return std::max(b, record_bytes<8, 8>(n_tiles[5]));
 }
 
 void tile_dims(int code, int* tx, int* ty)

@@ -7,6 +7,9 @@
 namespace sph {
 
 void tile_dims(int code, int* tx, int* ty);
+// Bytes of the per-tile staging records for the tile counts of every shape
+// (n_tiles indexed by tile code 1..SPH_TILE_COUNT).
+size_t stage_record_bytes(const int* n_tiles);
 // pdl: launch with programmatic stream serialization (the kernels wait on
 // their predecessor with griddepcontrol before reading its results).
 // tan: the forward-mode tangent variants (tile codes 1..4 only).
