@@ -273,6 +273,8 @@ TankDev make_tank_dev(const TankHost& t)
     d.cell = t.cell;
     d.m_body = p.m_body;
     d.J_body = p.J_body;
+    d.inv_m_body = 1.0 / p.m_body;
+    d.inv_J_body = 1.0 / p.J_body;
     d.dt_d = p.dt;
     d.grav_xd = p.grav_x;
     d.grav_yd = p.grav_y;

@@ -48,10 +48,12 @@ struct TankDev {
     int outer_every;
     double W, cell;               // grid half-width and cell side (FP64)
     double m_body, J_body, dt_d;
+    double inv_m_body, inv_J_body;
     double grav_xd, grav_yd;
 };
 
 struct BodyDev {
+    // the first eight doubles are read as an array by the body update
     double r[2], th, v[2], w;     // r, theta, rdot, thetadot at the current step
     double c, s;                  // cos(theta), sin(theta)
     double anchor[2][2];          // FP64 anchor of grid buffer 0 / 1

@@ -195,11 +195,10 @@ struct Red {
     unsigned long long pairs;
 };
 
-// Sums over the block (result valid in thread 0).  Only the parts flagged
-// by the uniform switches are reduced.
-__device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* >= 32 */)
+// Sums over a warp (result valid in lane 0).  Only the parts flagged by the
+// uniform switches are reduced.
+__device__ __forceinline__ Red warp_reduce(Red r, bool forces, bool com)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         if (forces) {
@@ -213,6 +212,14 @@ __device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* >= 32 
         }
         r.pairs += __shfl_down_sync(0xffffffffu, r.pairs, o);
     }
+    return r;
+}
+
+// Sums over the block (result valid in thread 0).
+__device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* one per warp */)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    r = warp_reduce(r, forces, com);
     __syncthreads();
     if (lane == 0) scratch[warp] = r;
     __syncthreads();
@@ -240,14 +247,15 @@ __device__ __forceinline__ void store_partial(TilePartial* P, const Red& r, int 
     P->c = make_int4(__float_as_int(r.cy.hi), __float_as_int(r.cy.lo), (int)r.pairs, wall);
 }
 
-// Block-wide sum of partials [p0, p1) in fixed order (result in thread 0);
-// *wall receives whether any of them saw a ghost pair (all threads).
-__device__ Red reduce_partials(const TilePartial* P, int p0, int p1, bool com, int* wall, Red* scratch)
+// Sum of partials [p0, p1) by one warp in fixed order: lane-strided, then a
+// shuffle tree (result in lane 0).  *wall receives whether any of them saw a
+// ghost pair (all lanes).
+__device__ Red warp_reduce_partials(const TilePartial* P, int p0, int p1, bool com, int* wall)
 {
     const F2 z{0.f, 0.f};
     Red r{z, z, z, z, z, 0ull};
     int w = 0;
-    for (int i = p0 + threadIdx.x; i < p1; i += blockDim.x) {
+    for (int i = p0 + (int)(threadIdx.x & 31); i < p1; i += 32) {
         const float4 a = __ldcg(&P[i].a), b = __ldcg(&P[i].b);
         const int4 c = __ldcg(&P[i].c);
         r.fx = f2_add(r.fx, F2{a.x, a.y});
@@ -260,54 +268,71 @@ __device__ Red reduce_partials(const TilePartial* P, int p0, int p1, bool com, i
         r.pairs += (unsigned long long)(unsigned)c.z;
         w |= c.w;
     }
-    *wall = __syncthreads_or(w);
-    return block_reduce(r, true, com, scratch);
+    *wall = __any_sync(0xffffffffu, w);
+    return warp_reduce(r, true, com);
 }
 
 // ---------------------------------------------------------------------------
 // Body update by the last CTA of a tank (Eq. 20, Eq. 28, outputs)
 // ---------------------------------------------------------------------------
+// Runs in warp 0 of the CTA that completed the tank's last reduction group.
+// The FP64 pipe of this GPU is narrow and every global access on the serial
+// path costs an L2 round trip, so the lanes load the body and input values
+// before the group partials are reduced (the loads overlap the reduction),
+// the body is updated in registers and stored once, and the masses enter as
+// reciprocals.
 __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
-                              bool sample, bool tan, Red* scratch)
+                              bool sample, bool tan)
 {
-    __threadfence();
+    fence_acq_rel();
     RunDev* run = S.run;
-    const long long step = run->step;
+    BodyDev* bp = S.body + tank;
+    const long long step = run->step, step0 = run->step0;
+    const long long k = step - step0;
+    // lane l loads one value: the body's r, theta, rdot, thetadot, cos, sin
+    // (l < 8, the leading doubles of BodyDev), the held control torque (8),
+    // the input (9..11); lane 0 collects them after the reduction
+    const int lane = (int)(threadIdx.x & 31);
+    const double* up = run->u;
+    double pre = 0.0;
+    if (lane < 8) pre = reinterpret_cast<const double*>(bp)[lane];
+    else if (lane == 8) pre = bp->tau_c;
+    else if (lane < 12 && up) pre = up[tank * run->u_tank_stride + 3 * k + (lane - 9)];
     int wall;
-    Red r = reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall, scratch);
+    Red r = warp_reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall);
     Red tr = r;
-    if (tan) tr = reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall, scratch);
-    if (threadIdx.x != 0) return;
+    if (tan) tr = warp_reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall);
+    double rx = __shfl_sync(0xffffffffu, pre, 0), ry = __shfl_sync(0xffffffffu, pre, 1);
+    double th = __shfl_sync(0xffffffffu, pre, 2), vx = __shfl_sync(0xffffffffu, pre, 3);
+    double vy = __shfl_sync(0xffffffffu, pre, 4), w = __shfl_sync(0xffffffffu, pre, 5);
+    double c = __shfl_sync(0xffffffffu, pre, 6), sn = __shfl_sync(0xffffffffu, pre, 7);
+    double tau_c = __shfl_sync(0xffffffffu, pre, 8);
+    const double ux = __shfl_sync(0xffffffffu, pre, 9), uy = __shfl_sync(0xffffffffu, pre, 10);
+    const double ut = __shfl_sync(0xffffffffu, pre, 11);
+    if (lane != 0) return;
+    const int ctrl_on = run->ctrl_on, body_fixed = run->body_fixed;
 
     // FP64 from here on: assembly of the reduced force/torque and the body
     const double Fx = (double)r.fx.hi + (double)r.fx.lo;
     const double Fy = (double)r.fy.hi + (double)r.fy.lo;
     const double Tq = (double)r.t.hi + (double)r.t.lo;
-    BodyDev& b = S.body[tank];
-    const long long k = step - run->step0;
-    double ux = 0.0, uy = 0.0, ut = 0.0;
-    if (run->u) {
-        const double* u = run->u + tank * run->u_tank_stride + 3 * k;
-        ux = u[0];
-        uy = u[1];
-        ut = u[2];
-    }
     if (sample) {
         const long long oe = T.outer_every;
-        const long long row = step / oe - (run->step0 + oe - 1) / oe;
-        if (run->ctrl_on) {  // Eq. 28 under zero-order hold
+        const long long row = step / oe - (step0 + oe - 1) / oe;
+        if (ctrl_on) {  // Eq. 28 under zero-order hold
             const double ref = run->theta_ref ? run->theta_ref[tank * run->ref_stride + row] : 0.0;
             const double Jc = run->ctrl_J > 0.0 ? run->ctrl_J : T.J_body;
-            b.tau_c = Jc * run->ctrl_w * run->ctrl_w * (ref - b.th) - 2.0 * run->ctrl_xi * Jc * run->ctrl_w * b.w;
+            tau_c = Jc * run->ctrl_w * run->ctrl_w * (ref - th) - 2.0 * run->ctrl_xi * Jc * run->ctrl_w * w;
+            bp->tau_c = tau_c;
         }
         if (run->y) {
             double* y = run->y + tank * run->y_tank_stride + row * SPH_NY;
-            y[0] = b.r[0];
-            y[1] = b.r[1];
-            y[2] = b.th;
-            y[3] = b.v[0];
-            y[4] = b.v[1];
-            y[5] = b.w;
+            y[0] = rx;
+            y[1] = ry;
+            y[2] = th;
+            y[3] = vx;
+            y[4] = vy;
+            y[5] = w;
             y[6] = Fx;
             y[7] = Fy;
             y[8] = Tq;
@@ -326,9 +351,10 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
             duy = du[1];
             dut = du[2];
         }
+        BodyDev& b = *bp;
         if (sample && run->dy) {
             const long long oe = T.outer_every;
-            const long long row = step / oe - (run->step0 + oe - 1) / oe;
+            const long long row = step / oe - (step0 + oe - 1) / oe;
             double* y = run->dy + tank * run->y_tank_stride + row * SPH_NY;
             y[0] = b.tr[0];
             y[1] = b.tr[1];
@@ -342,10 +368,10 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
             y[9] = T.n_f ? ((double)tr.cx.hi + (double)tr.cx.lo) / T.n_f : 0.0;
             y[10] = T.n_f ? ((double)tr.cy.hi + (double)tr.cy.lo) / T.n_f : 0.0;
         }
-        if (!run->body_fixed) {
-            b.tv[0] += T.dt_d * (dFx + dux) / T.m_body;
-            b.tv[1] += T.dt_d * (dFy + duy) / T.m_body;
-            b.tw += T.dt_d * (dTq + dut) / T.J_body;
+        if (!body_fixed) {
+            b.tv[0] += T.dt_d * (dFx + dux) * T.inv_m_body;
+            b.tv[1] += T.dt_d * (dFy + duy) * T.inv_m_body;
+            b.tw += T.dt_d * (dTq + dut) * T.inv_J_body;
             b.tr[0] += T.dt_d * b.tv[0];
             b.tr[1] += T.dt_d * b.tv[1];
             b.tth += T.dt_d * b.tw;
@@ -357,8 +383,8 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
         b.ftv[1] = (float)b.tv[1];
         b.ftw = (float)b.tw;
     }
-    const double tau = ut + (run->ctrl_on ? b.tau_c : 0.0);
-    const double ax = (Fx + ux) / T.m_body, ay = (Fy + uy) / T.m_body, aw = (Tq + tau) / T.J_body;
+    const double tau = ut + (ctrl_on ? tau_c : 0.0);
+    const double ax = (Fx + ux) * T.inv_m_body, ay = (Fy + uy) * T.inv_m_body, aw = (Tq + tau) * T.inv_J_body;
     if (eval) {
         if (E.body) {
             double* o = E.body + 6 * tank;
@@ -370,34 +396,46 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
             o[5] = aw;
         }
     } else {
-        b.anchor[nbuf][0] = b.r[0];
-        b.anchor[nbuf][1] = b.r[1];
-        if (!run->body_fixed) {
-            b.v[0] += T.dt_d * ax;  // kick then drift (Section 3.4)
-            b.v[1] += T.dt_d * ay;
-            b.w += T.dt_d * aw;
-            b.r[0] += T.dt_d * b.v[0];
-            b.r[1] += T.dt_d * b.v[1];
-            b.th += T.dt_d * b.w;
-            sincos(b.th, &b.s, &b.c);
+        bp->anchor[nbuf][0] = rx;
+        bp->anchor[nbuf][1] = ry;
+        if (!body_fixed) {
+            vx += T.dt_d * ax;  // kick then drift (Section 3.4)
+            vy += T.dt_d * ay;
+            w += T.dt_d * aw;
+            rx += T.dt_d * vx;
+            ry += T.dt_d * vy;
+            th += T.dt_d * w;
+            sincos(th, &sn, &c);
+            bp->v[0] = vx;
+            bp->v[1] = vy;
+            bp->w = w;
+            bp->r[0] = rx;
+            bp->r[1] = ry;
+            bp->th = th;
+            bp->s = sn;
+            bp->c = c;
         }
-        b.dc = df_split(b.c);
-        b.ds = df_split(b.s);
-        b.drx = df_split(b.r[0]);
-        b.dry = df_split(b.r[1]);
-        b.fvx = (float)b.v[0];
-        b.fvy = (float)b.v[1];
-        b.fw = (float)b.w;
-        b.fc = (float)b.c;
-        b.fs = (float)b.s;
-        b.frx = (float)b.r[0];
-        b.fry = (float)b.r[1];
-        b.fo_next[0] = (float)(b.r[0] - T.W);
-        b.fo_next[1] = (float)(b.r[1] - T.W);
-        b.pairs += r.pairs;
+        bp->dc = df_split(c);
+        bp->ds = df_split(sn);
+        bp->drx = df_split(rx);
+        bp->dry = df_split(ry);
+        bp->fvx = (float)vx;
+        bp->fvy = (float)vy;
+        bp->fw = (float)w;
+        bp->fc = (float)c;
+        bp->fs = (float)sn;
+        bp->frx = (float)rx;
+        bp->fry = (float)ry;
+        bp->fo_next[0] = (float)(rx - T.W);
+        bp->fo_next[1] = (float)(ry - T.W);
+        bp->pairs += r.pairs;
     }
-    b.done = 0;
-    __threadfence();
+    bp->done = 0;
+    if (S.B == 1) {  // the only tank: its step is the pass's (visible when the kernel completes)
+        if (!eval) run->step = step + 1;
+        return;
+    }
+    fence_acq_rel();
     const unsigned prev = atomicAdd(&run->tanks_done, 1u);
     if (prev == (unsigned)S.B - 1) {
         if (!eval) run->step = step + 1;
@@ -639,25 +677,25 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     if (threadIdx.x == 0) {
         store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
         if constexpr (TAN) store_partial(S.tpartials + blockIdx.x, tr, any_wall ? 1 : 0);
-        __threadfence();
+        fence_acq_rel();
         is_last = (atomicAdd(&S.gdone[g], 1u) == (unsigned)(gt1 - gt0 - 1));
     }
     __syncthreads();
-    if (!is_last) return;
-    __threadfence();
+    if (!is_last || threadIdx.x >= 32) return;  // warp 0 of the group's last tile goes on
+    fence_acq_rel();
     int wall_g;
-    r = reduce_partials(S.partials, gt0, gt1, sample, &wall_g, scratch);
-    if constexpr (TAN) tr = reduce_partials(S.tpartials, gt0, gt1, sample, &wall_g, scratch);
+    r = warp_reduce_partials(S.partials, gt0, gt1, sample, &wall_g);
+    if constexpr (TAN) tr = warp_reduce_partials(S.tpartials, gt0, gt1, sample, &wall_g);
+    unsigned prev = 0;
     if (threadIdx.x == 0) {
         store_partial(S.gpartials + g, r, wall_g);
         if constexpr (TAN) store_partial(S.tgpartials + g, tr, wall_g);
         S.gdone[g] = 0;
-        __threadfence();
-        const unsigned n_groups = (unsigned)(S.group_first[tank + 1] - S.group_first[tank]);
-        is_last = (atomicAdd(&S.body[tank].done, 1u) == n_groups - 1);
+        fence_acq_rel();
+        prev = atomicAdd(&S.body[tank].done, 1u);
     }
-    __syncthreads();
-    if (is_last) tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN, scratch);
+    const unsigned n_groups = (unsigned)(S.group_first[tank + 1] - S.group_first[tank]);
+    if (__shfl_sync(0xffffffffu, prev, 0) == n_groups - 1) tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,6 +29,12 @@ struct Shape {
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Release/acquire fence at GPU scope: orders this thread's earlier memory
+// accesses before its later ones as seen by other CTAs (lighter than the
+// sequentially consistent __threadfence).  With a relaxed atomic counter it
+// publishes data (store; fence; atomic) and consumes it (atomic; fence; load).
+__device__ __forceinline__ void fence_acq_rel() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
 // ---------------------------------------------------------------------------
 // Shared-memory staging of a tile and its halo
 // ---------------------------------------------------------------------------
