@@ -230,6 +230,30 @@ int sph_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv0, 
             double* y_out, double* dy_out, float* dxv_out, double* dbody_out, void* stream);
 
 /*
+ * Jacobian-vector product of the continuous dynamics xdot = f(x, u)
+ * (Section 5.2, the linearisation of Algorithm 1) at the current state, with
+ * the neighbour set of the current step and no controller; the state is not
+ * advanced.  Given the tangent of the state and of the input:
+ *  u          float64 [B, 3] input (NULL: zero), device
+ *  du         float64 [B, 3] input tangent (NULL: zero), device
+ *  dxv        float32 [N, 4] fluid state tangent (dx, dy, dvx, dvy) in the
+ *             order of sph_get_state (NULL: zero), device
+ *  dbody      float64 [B, 6] body state tangent (r, theta, rdot, thetadot
+ *             components as in sph_get_state; NULL: zero), device
+ * returns the tangent of the fluid accelerations
+ *  dacc       float32 [N, 2] out (NULL: skip), device
+ * and of the body's F_x, F_y, T_b (Eq. 20 fluid terms) and rddot_x,
+ * rddot_y, thetaddot (Eq. 20 with u)
+ *  dbody_acc  float64 [B, 6] out (NULL: skip), device.
+ * The position rows of f are the velocities themselves, so (dxv, dbody) and
+ * these outputs give A v = (df/dx) v whole.  Tangent kernels exist for tile
+ * shapes up to 8x4 (a larger shape is replaced by 8x4 for this call).
+ * Allocates the tangent buffers on first use.
+ */
+int sph_eval_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv, const double* dbody,
+                 float* dacc, double* dbody_acc, void* stream);
+
+/*
  * Reverse-mode (adjoint) derivative of K steps: the transpose of the map
  * sph_jvp linearises (Section 3.5, Jacobians of the simulator), no
  * controller, the neighbour set of each step frozen.  From the current state

@@ -75,6 +75,7 @@ def _declare(L):
         "sph_autotune": ([vp, i32, ip, dp, vp], C.c_int),
         "sph_relax": ([vp, i32, C.c_double, vp], C.c_int),
         "sph_jvp": ([vp, vp, vp, vp, vp, i32, vp, vp, vp, vp, vp], C.c_int),
+        "sph_eval_jvp": ([vp, vp, vp, vp, vp, vp, vp, vp], C.c_int),
         "sph_vjp": ([vp, vp, i32, vp, vp, vp, vp, vp, vp, i32, vp], C.c_int),
         "sph_time_kernels": ([vp, i32, dp, vp], C.c_int),
         "sph_run_batch": ([P, i32, vp, i32, C.POINTER(SphCtrl), vp, ip, vp], C.c_int),

@@ -75,3 +75,74 @@ def rollout(params: dict, xv0, body0, u, checkpoint_every: int = 10):
     if not torch.is_tensor(u):
         u = torch.as_tensor(u, dtype=torch.float64)
     return _Rollout.apply(u, body0, xv0, params, checkpoint_every)
+
+
+# ---------------------------------------------------------------------------
+# Linearization of the dynamics (Section 5.2): the Jacobian of xdot = f(x, u)
+# and its eigenvalues along a trajectory
+# ---------------------------------------------------------------------------
+def state_index(n_f: int) -> dict:
+    """Layout of the state vector x (n = 4 n_f + 6): the fluid state flattened
+    row-major (x, y, vx, vy per particle, in the order of Sim.state), then the
+    body (r_x, r_y, theta, rdot_x, rdot_y, thetadot).  Returns the indices of
+    the positions and of their velocities, pairwise."""
+    fl = torch.arange(4 * n_f).reshape(n_f, 4)
+    pos = torch.cat([fl[:, :2].reshape(-1), 4 * n_f + torch.arange(3)])
+    vel = torch.cat([fl[:, 2:].reshape(-1), 4 * n_f + 3 + torch.arange(3)])
+    return dict(n=4 * n_f + 6, pos=pos, vel=vel)
+
+
+def jacobian(params: dict, xv, body, u=None, block: int = 256) -> torch.Tensor:
+    """A = df/dx [n, n] (float64, CUDA) of the continuous dynamics
+    xdot = f(x, u) of one tank at the state (xv [N, 4], body [6]) and input
+    u [3], open loop, in the layout of state_index.  The position rows are the
+    identity on the velocity columns; the velocity rows come from
+    Jacobian-vector products (Sim.eval_jvp) of a batch of ``block`` copies of
+    the tank, copy i carrying the unit tangent of one column."""
+    xv = torch.as_tensor(xv, dtype=torch.float32).reshape(-1, 4).cuda()
+    body = torch.as_tensor(body, dtype=torch.float64).reshape(6).cuda()
+    n_f = xv.shape[0]
+    ix = state_index(n_f)
+    n = ix["n"]
+    u1 = None if u is None else torch.as_tensor(u, dtype=torch.float64).reshape(1, 3).cuda()
+    nb = max(1, min(block, n))
+    A = torch.zeros((n, n), dtype=torch.float64, device="cuda")
+    A[ix["pos"].cuda(), ix["vel"].cuda()] = 1.0
+    vel_f = torch.arange(4 * n_f, device="cuda").reshape(n_f, 4)[:, 2:].reshape(-1)
+    with Sim([params] * nb) as sim:
+        sim.set_state(xv.repeat(nb, 1), body.repeat(nb, 1))
+        for c0 in range(0, n, nb):
+            cols = torch.arange(c0, min(c0 + nb, n), device="cuda")
+            k = cols.numel()
+            dxv = torch.zeros((nb, n_f * 4), dtype=torch.float32, device="cuda")
+            db = torch.zeros((nb, 6), dtype=torch.float64, device="cuda")
+            fl = cols < 4 * n_f
+            rows = torch.arange(k, device="cuda")
+            dxv[rows[fl], cols[fl]] = 1.0
+            db[rows[~fl], cols[~fl] - 4 * n_f] = 1.0
+            dacc, dba = sim.eval_jvp(dxv.reshape(nb * n_f, 4), db, u=None if u1 is None else u1.repeat(nb, 1))
+            sim.check()
+            A[vel_f, c0:c0 + k] = dacc.reshape(nb, 2 * n_f)[:k].T.double()
+            A[4 * n_f + 3:, c0:c0 + k] = dba[:k, 3:].T
+    return A
+
+
+def eigenvalues_over_time(params: dict, xv0, body0, u, at_steps, block: int = 256):
+    """Eigenvalues of A = df/dx at the given step indices of the open-loop
+    trajectory from (xv0, body0) under the inputs u [K, 3].  Returns a list of
+    complex [n] tensors (CPU)."""
+    at = sorted(int(k) for k in at_steps)
+    u = torch.as_tensor(u, dtype=torch.float64).reshape(-1, 3).cuda()
+    out = []
+    with Sim(params) as sim:
+        sim.set_state(torch.as_tensor(xv0, dtype=torch.float32), torch.as_tensor(body0, dtype=torch.float64))
+        k = 0
+        for ka in at:
+            if ka > k:
+                sim.step(ka - k, u=u[k:ka][None], record=False)
+                k = ka
+            xv, body = sim.state()
+            sim.check()
+            A = jacobian(params, xv, body[0], u[ka] if ka < u.shape[0] else None, block=block)
+            out.append(torch.linalg.eigvals(A.cpu()))  # host LAPACK (a dense nonsymmetric eigensolver)
+    return out

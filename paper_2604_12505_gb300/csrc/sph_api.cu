@@ -625,6 +625,46 @@ int sph_relax(sph_sim* sim, int32_t n_steps, double damping, void* stream)
     return SPH_OK;
 }
 
+namespace {
+// Tangent buffers of the forward-mode kernels, allocated on first use.
+int ensure_tangent(sph_sim* sim)
+{
+    if (sim->S.trho) return SPH_OK;
+    const size_t nslot = (size_t)sim->n_cells_total * kCap;
+    int rc = SPH_OK;
+    for (int b = 0; b < 2; ++b) rc |= dalloc(&sim->S.tpv[b], nslot);
+    rc |= dalloc(&sim->S.trho, nslot);
+    rc |= dalloc(&sim->S.tgh, sim->n_g_total);
+    rc |= dalloc(&sim->S.tpartials, sim->max_tiles);
+    rc |= dalloc(&sim->S.tgpartials, sim->max_groups);
+    return rc ? SPH_E_NOMEM : SPH_OK;
+}
+}  // namespace
+
+int sph_eval_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv, const double* dbody,
+                 float* dacc, double* dbody_acc, void* stream)
+{
+    if (!sim) return fail(SPH_E_INVAL, "sph_eval_jvp: NULL handle");
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_tangent(sim);
+    if (rc) return rc;
+    const int code = sim->tile_code > 4 ? 4 : sim->tile_code;  // tangent kernels exist for tiles up to 8x4
+    const SimDev S = sim->dev(code);
+    const int buf = (int)(sim->host_step & 1);
+    CK(launch_tangent_state(S, dxv, nullptr, dbody, nullptr, sim->n_cells_total, buf, st));
+    RunDev d{};
+    d.u = u;
+    d.du = du;
+    d.u_tank_stride = 3;
+    CK(launch_set_run(sim->d_run, d, st));
+    EvalOut E{};
+    E.dacc = dacc;
+    E.dbody = dbody_acc;
+    cudaError_t e = launch_step(S, E, 1, code, sim->n_tiles[code], st, false, true);
+    if (e != cudaSuccess) return fail(SPH_E_CUDA, std::string("sph_eval_jvp launch: ") + cudaGetErrorString(e));
+    return SPH_OK;
+}
+
 int sph_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv0, const double* dbody0, int32_t K,
             double* y_out, double* dy_out, float* dxv_out, double* dbody_out, void* stream)
 {
@@ -633,16 +673,8 @@ int sph_jvp(sph_sim* sim, const double* u, const double* du, const float* dxv0, 
         if (sim->tanks[b].p.outer_every != sim->tanks[0].p.outer_every)
             return fail(SPH_E_UNSUPPORTED, "sph_jvp: tanks of a batch must share outer_every");
     cudaStream_t st = (cudaStream_t)stream;
-    if (!sim->S.trho) {  // tangent buffers, allocated on first use
-        const size_t nslot = (size_t)sim->n_cells_total * kCap;
-        int rc = SPH_OK;
-        for (int b = 0; b < 2; ++b) rc |= dalloc(&sim->S.tpv[b], nslot);
-        rc |= dalloc(&sim->S.trho, nslot);
-        rc |= dalloc(&sim->S.tgh, sim->n_g_total);
-        rc |= dalloc(&sim->S.tpartials, sim->max_tiles);
-        rc |= dalloc(&sim->S.tgpartials, sim->max_groups);
-        if (rc) return SPH_E_NOMEM;
-    }
+    int rc = ensure_tangent(sim);
+    if (rc) return rc;
     const int code = sim->tile_code > 4 ? 4 : sim->tile_code;  // tangent kernels exist for tiles up to 8x4
     const SimDev S = sim->dev(code);
     const int buf = (int)(sim->host_step & 1);

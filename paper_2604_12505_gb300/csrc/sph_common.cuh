@@ -158,6 +158,8 @@ struct EvalOut {
     int* nbr;         // [N, 3]
     int* keys;        // [N]
     double* body;     // [B, 6]
+    float* dacc;      // tangent variant: [N, 2] tangent of the fluid acceleration
+    double* dbody;    // tangent variant: [B, 6] tangent of body_out
 };
 
 // Pointers of one simulator instance, passed by value to every kernel.

@@ -383,6 +383,25 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
         b.ftv[1] = (float)b.tv[1];
         b.ftw = (float)b.tw;
     }
+    if (tan && eval && E.dbody) {  // tangent of the evaluation's body outputs (no controller)
+        const double dFx = (double)tr.fx.hi + (double)tr.fx.lo;
+        const double dFy = (double)tr.fy.hi + (double)tr.fy.lo;
+        const double dTq = (double)tr.t.hi + (double)tr.t.lo;
+        double dux = 0.0, duy = 0.0, dut = 0.0;
+        if (run->du) {
+            const double* du = run->du + tank * run->u_tank_stride + 3 * k;
+            dux = du[0];
+            duy = du[1];
+            dut = du[2];
+        }
+        double* o = E.dbody + 6 * tank;
+        o[0] = dFx;
+        o[1] = dFy;
+        o[2] = dTq;
+        o[3] = (dFx + dux) * T.inv_m_body;
+        o[4] = (dFy + duy) * T.inv_m_body;
+        o[5] = (dTq + dut) * T.inv_J_body;
+    }
     const double tau = ut + (ctrl_on ? tau_c : 0.0);
     const double ax = (Fx + ux) * T.inv_m_body, ay = (Fy + uy) * T.inv_m_body, aw = (Tq + tau) * T.inv_J_body;
     if (eval) {
@@ -622,6 +641,12 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 if (E.acc) {
                     E.acc[2 * id] = ax;
                     E.acc[2 * id + 1] = ay;
+                }
+                if constexpr (TAN) {
+                    if (E.dacc) {
+                        E.dacc[2 * id] = tax;
+                        E.dacc[2 * id + 1] = tay;
+                    }
                 }
                 if (E.nbr) {
                     E.nbr[3 * id] = nff;

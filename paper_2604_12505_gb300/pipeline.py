@@ -135,16 +135,33 @@ def _closed_loop_inputs(B: int, K: int, Ts: float, seed0: int):
     return F, tau, ref
 
 
+def identification_inputs(B: int, K: int, Ts: float, seed0: int) -> np.ndarray:
+    """[B, K, 3] identification trains (Section 5.3.1), one per tank, with the
+    paper's design scaled from its 2200 samples of 0.05 s (110 s) to a horizon
+    of K samples of Ts: the multisine keeps its 39 lines with the resolution
+    of one period over its segment (the paper's 0.05 Hz over 82.5 s), and the
+    pulse widths and rests shrink by the same factor."""
+    from . import workloads as W
+
+    horizon = K * Ts
+    scale = horizon / (2200 * 0.05)
+    f_res = 1.0 / (0.75 * horizon)
+    return np.stack([W.identification_train(K, Ts, seed=seed0 + b, f_res=f_res, f_max=40 * f_res,
+                                            pulse_width=(0.25 * scale, 1.0 * scale),
+                                            pulse_rest=(1.0 * scale, 4.0 * scale)) for b in range(B)])
+
+
 def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, relax: int = 5000,
                     dt: float = 2e-4, cl_tanks: int = 64, cl_steps: int = 5000, n_sims: int = 65_536,
                     fit_cfg: dict | None = None, seq_tanks: int = 8, seq_steps: int = 1000, ctrl=None,
-                    log=None) -> dict:
+                    log=None, inputs: str = "piecewise") -> dict:
     """The surrogate workflow on the simulator and the LPV library.
 
     1. D_N: n_tanks tanks (fill, dx from the data-set distribution) relaxed
        once, ``launches`` open-loop runs of ``steps`` steps each with seeded
-       piecewise-constant inputs; the batch step rate against the same tanks
-       stepped one at a time.
+       inputs -- piecewise-constant holds (``inputs="piecewise"``) or the
+       identification train scaled to the horizon (``inputs="train"``); the
+       batch step rate against the same tanks stepped one at a time.
     2. Fit (lpv.fit) on the trajectories of the first 80 % of the tanks, for
        the LPV model (p = [fill, thetadot]) and the LTI model (no scheduling).
     3. cl_tanks unseen tanks under unseen manoeuvres in closed loop with the PD
@@ -165,8 +182,14 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
     t0 = time.perf_counter()
     tanks = Tanks(params, relax)
     out["relax_wall_s"] = time.perf_counter() - t0
-    u_l = [np.stack([W.piecewise_profile(K, Ts, seed=100_000 + 1000 * l + b) for b in range(n_tanks)])
-           for l in range(launches)]
+    if inputs == "piecewise":
+        u_l = [np.stack([W.piecewise_profile(K, Ts, seed=100_000 + 1000 * l + b) for b in range(n_tanks)])
+               for l in range(launches)]
+    elif inputs == "train":
+        u_l = [identification_inputs(n_tanks, K, Ts, seed0=100_000 + 1000 * l) for l in range(launches)]
+    else:
+        raise ValueError(f"inputs must be 'piecewise' or 'train', not {inputs!r}")
+    out["inputs"] = inputs
     d = dataset(tanks, u_l)
     npart = np.array(tanks.n_fluid, dtype=np.float64)
     seq = sequential_rate(tanks, list(range(min(seq_tanks, n_tanks))), seq_steps)
@@ -245,3 +268,64 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
                              speedup=(n_sims / lpv_s) / (cl_tanks / sph_s), steps=cl_steps, periods=Kc, Ts=Ts, dt=dt)
     say("throughput", out["throughput"])
     return out
+
+
+def linearization_study(cfg: dict | None = None, relax: int = 2000, steps: int = 2000, n_points: int = 3,
+                        tau: float = 5.0, block: int = 1024, log=None) -> dict:
+    """Eigenvalues of the linearised dynamics along a manoeuvre (Section 5.2,
+    the Jacobian of xdot = f(x, u) by automatic differentiation): the tank
+    (by default the paper's benchmark spacecraft) relaxed to rest, then a
+    torque slew (+tau, then -tau) of ``steps`` steps; A = df/dx at n_points
+    evenly spaced steps from the library's Jacobian-vector products, and its
+    spectrum.  Reports the timings and, per point, the spectral abscissa
+    (largest real part), the spectral radius and the number of eigenvalues
+    with real part above 1e-6 of the radius."""
+    from . import autodiff as AD
+    from . import workloads as W
+    from .sph import Sim
+
+    say = log or (lambda *a: None)
+    cfg = dict(cfg or W.PAPER)
+    with Sim(cfg) as sim:
+        sim.relax(relax, damping=2e-3)
+        xv, body = sim.state()
+        xv[:, 2:] = 0.0
+        n_f = xv.shape[0]
+    u = W.bang_bang_slew(steps, cfg["dt"], tau=tau, t1=steps * cfg["dt"] / 2)
+    at = np.linspace(0, steps, n_points).round().astype(int)
+    out = dict(particles=n_f, n=4 * n_f + 6, steps=steps, dt=cfg["dt"], points=[])
+    with Sim(cfg) as sim:
+        sim.set_state(xv, body[0])
+        k = 0
+        for ka in at:
+            if ka > k:
+                sim.step(int(ka - k), u=torch.tensor(u[k:ka], device="cuda")[None], record=False)
+                k = int(ka)
+            x, b = sim.state()
+            sim.check()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            A = AD.jacobian(cfg, x, b[0], u[ka] if ka < steps else None, block=block)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            ev = torch.linalg.eigvals(A.cpu())  # host LAPACK (a dense nonsymmetric eigensolver)
+            t2 = time.perf_counter()
+            re, mag = ev.real, ev.abs()
+            rad = mag.max().item()
+            pt = dict(step=int(ka), t=float(ka * cfg["dt"]), jacobian_s=t1 - t0, eig_s=t2 - t1,
+                      abscissa=re.max().item(), radius=rad, n_unstable=int((re > 1e-6 * rad).sum().item()),
+                      theta=float(b[0, 2].item()))
+            out["points"].append(pt)
+            say("linearization", pt)
+    return out
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+
+    if len(sys.argv) > 1 and sys.argv[1] == "linearize":
+        print(json.dumps(linearization_study(log=lambda *a: print(*a, file=sys.stderr))))
+    else:
+        print("usage: python -m paper_2604_12505_gb300.pipeline linearize", file=sys.stderr)
+        sys.exit(2)

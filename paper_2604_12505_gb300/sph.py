@@ -204,6 +204,20 @@ class Sim:
                              _ptr(out["nbr"]), _ptr(out["keys"]), _ptr(out["body"]), _stream(stream)), "sph_eval")
         return out
 
+    def eval_jvp(self, dxv=None, dbody=None, u=None, du=None, stream=None):
+        """Jacobian-vector product of the continuous dynamics at the current
+        state (sph_eval_jvp): tangents of the fluid accelerations [N, 2] and
+        of the body's (F_x, F_y, T_b, rddot_x, rddot_y, thetaddot) [B, 6]."""
+        dxv = None if dxv is None else _dev(dxv, torch.float32).reshape(self.n_total, 4)
+        dbody = None if dbody is None else _dev(dbody, torch.float64).reshape(self.B, 6)
+        u = None if u is None else _dev(u, torch.float64).reshape(self.B, 3)
+        du = None if du is None else _dev(du, torch.float64).reshape(self.B, 3)
+        dacc = torch.empty((self.n_total, 2), dtype=torch.float32, device="cuda")
+        dba = torch.empty((self.B, 6), dtype=torch.float64, device="cuda")
+        check(lib().sph_eval_jvp(self._h, _ptr(u), _ptr(du), _ptr(dxv), _ptr(dbody), _ptr(dacc), _ptr(dba),
+                                 _stream(stream)), "sph_eval_jvp")
+        return dacc, dba
+
     # -- diagnostics --------------------------------------------------------------
     def check(self, reset: bool = False, raise_on_error: bool = True, stream=None) -> int:
         f = C.c_int32()

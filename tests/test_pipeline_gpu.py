@@ -61,3 +61,14 @@ def test_small_surrogate_study_end_to_end():
     th = r["throughput"]
     assert th["surrogate_sims"] == 2048 and th["periods"] == 100
     assert th["surrogate_sims_per_s"] > th["sph_sims_per_s"]
+
+
+@pytest.mark.gpu
+def test_study_on_the_identification_train():
+    need_gpu()
+    from paper_2604_12505_gb300 import pipeline as PL
+    r = PL.surrogate_study(n_tanks=10, launches=1, steps=1000, relax=1000, cl_tanks=5, cl_steps=1000, n_sims=1024,
+                           fit_cfg=dict(adam_iters=20, restarts=1), seq_tanks=2, seq_steps=100, inputs="train")
+    assert r["inputs"] == "train" and r["dataset"]["trajectories"] == 10
+    for name in ("lpv", "lti", "no_fluid"):
+        assert all(np.isfinite(v) for v in r[f"closed_loop_{name}"]["nrmse"].values())
