@@ -90,12 +90,19 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
         int nn = 0;
         const float xlo = pi.x - T.clip, xhi = pi.x + T.clip;
+        // each cell is sorted by x: of the row's left cell only the suffix
+        // with x >= x_i - clip, of its right cell only the prefix with
+        // x < x_i + clip can lie within the support (clip = 2h (1 + 1e-3)
+        // keeps every FP32 decision r^2 < (2h)^2 inside the range).
+        // Branch-free candidate loop: the support test r^2 < (2h)^2 splits
+        // almost every warp, so the kernel value is computed for every
+        // candidate and selected by the test.  For q = r / h,
+        // f(q) = (2 - q)^3 - 4 max(1 - q, 0)^3 is Eq. 22's bracket on [0, 2)
+        // (W = sigma / h^2 f); r = r^2 rsqrt(max(r^2, FLT_MIN)) is exactly 0
+        // for the particle itself, giving W(0) = 4 sigma / h^2.  The tangent
+        // variant runs the same arithmetic, so its primal equals the step's.
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
-            // each cell is sorted by x: of the row's left cell only the suffix
-            // with x >= x_i - clip, of its right cell only the prefix with
-            // x < x_i + clip can lie within the support (clip = 2h (1 + 1e-3)
-            // keeps every FP32 decision r^2 < (2h)^2 inside the range)
             const int cl = c + dy * Sh::SX - 1;
             const int a = lower_x(sm, sm.start[cl], sm.start[cl + 1], xlo);
             const int z = lower_x(sm, sm.start[cl + 2], sm.start[cl + 3], xhi);
@@ -103,25 +110,27 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 const float4 pj = sm.pv[j];
                 const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);
                 const float r2 = dist2(ddx, ddy);
-                if (r2 < T.R2) {
-                    const float inv_r = rsqrtf(r2);
-                    const float r = r2 * inv_r;
-                    Sf += (r2 > 0.f) ? w_cubic(T, r) : T.cW * 4.0f;
-                    if (j != e) {
-                        if (rec && nn < kNbrMax) lst[nn * Sh::MAXOWN] = (unsigned short)j;
-                        ++nn;
-                        if (want_drho && r2 > 0.f)
-                            Df += ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * dw_cubic_over_r(T, r, inv_r);
-                        if constexpr (TAN) {
-                            if (r2 > 0.f) {
-                                const float4 tj = sm.tpv[j];
-                                dRf += (ddx * (ti.x - tj.x) + ddy * (ti.y - tj.y)) * dw_cubic_over_r(T, r, inv_r);
-                            }
-                        }
+                const bool in = r2 < T.R2;
+                const float inv_r = rsqrtf(fmaxf(r2, FLT_MIN));
+                const float q = r2 * inv_r * T.inv_h;
+                const float qa = 2.0f - q, qb = fmaxf(1.0f - q, 0.0f);
+                const float f = fmaf(-4.0f * qb * qb, qb, qa * qa * qa);
+                Sf += in ? f : 0.0f;
+                const bool nb = in && (j != e);
+                if (nb && rec && nn < kNbrMax) lst[nn * Sh::MAXOWN] = (unsigned short)j;
+                nn += nb ? 1 : 0;
+                const bool nd = nb && r2 > 0.f;
+                if (want_drho || TAN) {
+                    const float gW = T.cdW * fmaf(12.0f * qb, qb, -3.0f * qa * qa) * inv_r;  // (dW/dr) / r
+                    if (want_drho) Df += nd ? ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * gW : 0.0f;
+                    if constexpr (TAN) {
+                        const float4 tj = sm.tpv[j];
+                        dRf += nd ? (ddx * (ti.x - tj.x) + ddy * (ti.y - tj.y)) * gW : 0.0f;
                     }
                 }
             }
         }
+        Sf *= T.cW;
         if (rec) S.nbn[blockIdx.x * Sh::MAXOWN + t] = (unsigned char)min(nn, 255);
         float Sg = 0.f, Dg = 0.f;
         int ng2 = 0;
