@@ -59,8 +59,9 @@ enum {
  *  - fluid particles sit on the lattice ((i+1/2)dx, (j+1/2)dx) inside the
  *    disk of radius R - dx/2 and below the chord whose circular segment has
  *    area fill * pi * R^2; ghost particles sit on n_rings rings of radius
- *    R + (k+1/2)dx, round(2 pi r_k / dx) per ring, fixed in the body frame
- *    (Section 3.2, Eq. 21);
+ *    R + (k+1/2) s_g, round(2 pi r_k / s_g) per ring, fixed in the body
+ *    frame (Section 3.2, Eq. 21), with s_g = ghost_spacing * dx (Table 2's
+ *    single layer of ghosts is 0.9 times as long as a fluid particle);
  *  - fluid and ghosts share the mass m = rho0 * dx^2, h = h_over_dx * dx;
  *  - sigma_cubic <= 0 selects the normalised cubic-spline constant
  *    5/(14 pi) (Eq. 22 prints 15/(14 pi), whose 2-D integral is 3);
@@ -88,6 +89,7 @@ typedef struct sph_params {
     double ghost_pressure_sign; /* -1 (default reading) or +1 (literal)       */
     int32_t n_rings;            /* ghost rings (>= 1)                         */
     int32_t outer_every;        /* inner steps per sampling period T_s (>= 1) */
+    double ghost_spacing;       /* ghost spacing s_g over dx; <= 0 selects 1  */
 } sph_params;
 
 /*
@@ -306,6 +308,23 @@ int sph_time_kernels(sph_sim* sim, int32_t n_steps, double* us, void* stream);
  */
 int sph_run_batch(const sph_params* p, int32_t B, const double* u_profiles, int32_t T, const sph_ctrl* pd,
                   double* y_out, int32_t* n_particles_out, void* stream);
+
+/*
+ * Boundary correcting factor gamma1 of Eq. 14, estimated by Eq. 15 for a
+ * representative wall configuration (Section 3.5; the boundary sketch of
+ * Section 3.2): a straight wall, the fluid lattice of spacing dx on one side
+ * (rows at (b + 1/2) dx, b >= 0), the n_rings ghost rows of spacing s_g =
+ * ghost_spacing * dx on the other (rows at -(k + 1/2) s_g), and the particle
+ * in the first fluid row.  rho_i / m_i is the kernel sum of an interior
+ * particle of the same lattice, and the ghost sum is averaged over the
+ * offset of the ghost rows along the wall:
+ *   gamma1 = (sum_lattice W - sum_fluid W) / mean sum_ghost W   (Eq. 22 W).
+ * Uses h_over_dx, dx, ghost_spacing, n_rings and sigma_cubic of *p (host);
+ * writes *gamma1 (host).  Host computation only, no device work.
+ * SPH_E_INVAL: NULL pointer, dx or h_over_dx not positive, n_rings < 1, or
+ * no ghost row within the support.
+ */
+int sph_gamma1_estimate(const sph_params* p, double* gamma1);
 
 /*
  * Density without any memory allocation.  The paper has no counterpart: this

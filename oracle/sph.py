@@ -51,6 +51,7 @@ class Params(C.Structure):
         ("ctrl_xi", C.c_double),
         ("n_rings", C.c_int32),
         ("outer_every", C.c_int32),
+        ("ghost_spacing", C.c_double),
     ]
 
 
@@ -157,6 +158,53 @@ def dw_spiky(r, h):
 
 def fill_chord(R, fill):
     return lib().orc_fill_chord(float(R), float(fill))
+
+
+# --- boundary correcting factor (Eq. 15, Section 3.5) ----------------------
+def gamma1_estimate(p: Params, phase=None, n_phase: int = 512) -> float:
+    """Eq. 15's gamma1 for the reference wall described in gamma1_terms."""
+    lattice, fluid, ghost = gamma1_terms(p, phase, n_phase)
+    return (lattice - fluid) / ghost
+
+
+def gamma1_terms(p: Params, phase=None, n_phase: int = 512):
+    """The three kernel sums of Eq. 15 (lattice, fluid, ghost; see below).
+
+    Eq. 15 for the reference wall configuration of the boundary sketch
+    (Section 3.2), precomputed as Section 3.5 describes.
+
+    A straight wall along y = 0.  Fluid on the lattice (a dx, (b + 1/2) dx),
+    b >= 0; n_rings ghost layers on the lines y = -(k + 1/2) s_g with ghosts
+    at x = (c + phase) s_g (s_g the ghost spacing); the particle i sits at
+    (0, dx/2) in the first fluid row.  rho_i / m_i is the kernel sum of an
+    interior particle of the same lattice (the density the fluid has away
+    from the wall), so Eq. 15 reads
+        gamma1 = (sum_lattice W - sum_f W_i,f) / sum_g W_i,g.
+    phase=None averages the ghost sum over n_phase equispaced phases in
+    [0, 1): along a ring the ghosts' offset against the lattice varies.
+    """
+    L = lib()
+    dx, h = p.dx, h_of(p)
+    sg = (p.ghost_spacing if p.ghost_spacing > 0 else 1.0) * dx
+    sigma = p.sigma_cubic if p.sigma_cubic > 0 else 5.0 / (14.0 * np.pi)
+    n = int(np.ceil(2.0 * h / dx)) + 1
+    full = fluid = 0.0
+    for a in range(-n, n + 1):
+        for b in range(-n, n + 1):
+            w = L.orc_w_cubic(dx * float(np.hypot(a, b)), h, sigma)
+            full += w
+            if b >= 0:
+                fluid += w
+    phases = [phase] if phase is not None else [(q + 0.5) / n_phase for q in range(n_phase)]
+    nc = int(np.ceil(2.0 * h / sg)) + 2
+    ghost = 0.0
+    for ph in phases:
+        for k in range(p.n_rings):
+            yk = -(k + 0.5) * sg - 0.5 * dx
+            for c in range(-nc, nc + 1):
+                ghost += L.orc_w_cubic(float(np.hypot((c + ph) * sg, yk)), h, sigma)
+    ghost /= len(phases)
+    return full, fluid, ghost
 
 
 # --- tank (reading R9) -----------------------------------------------------

@@ -42,7 +42,8 @@
  *  R9 Tank construction: fluid on the lattice ((i+1/2)dx, (j+1/2)dx) inside
  *     the disk of radius R - dx/2 and below the chord whose circular segment
  *     has area fill * pi R^2; ghosts on n_rings rings of radius
- *     R + (k+1/2)dx with round(2 pi r_k / dx) equispaced particles each.
+ *     R + (k+1/2) s_g with round(2 pi r_k / s_g) equispaced particles each,
+ *     s_g = ghost_spacing * dx (Table 2's single layer: 0.9 dx).
  *  R10 The "continuity sum" is the time derivative of Eq. 14 along the
  *     kinematic motion: m sum_f v_if . grad W + gamma1 m sum_g v_ig . grad W.
  */
@@ -83,11 +84,17 @@ typedef struct {
     double ctrl_xi;      /* controller damping xi of Eq. 28                 */
     int32_t n_rings;     /* number of ghost rings                           */
     int32_t outer_every; /* inner steps per sampling period T_s             */
+    double ghost_spacing; /* ghost spacing over dx (Table 2: 0.9); <= 0: 1  */
 } orc_params;
 
 #define ORC_NY 11 /* r_x r_y theta v_x v_y omega F_x F_y T c_x c_y */
 
 static double orc_h(const orc_params* p) { return p->h_over_dx * p->dx; }
+/* Ghost spacing s_g along a ring and between rings (R9). */
+static double orc_ghost_ds(const orc_params* p)
+{
+    return (p->ghost_spacing > 0.0 ? p->ghost_spacing : 1.0) * p->dx;
+}
 static double orc_mass(const orc_params* p) { return p->rho0 * p->dx * p->dx; }
 static double orc_sigma(const orc_params* p)
 {
@@ -190,10 +197,11 @@ static int fluid_keep(const orc_params* p, double c, int i, int j, double* px, d
     return (r2 <= rin * rin) && (y <= c);
 }
 
+static double ring_radius(const orc_params* p, int k) { return p->R + ((double)k + 0.5) * orc_ghost_ds(p); }
+
 static int ring_count(const orc_params* p, int k)
 {
-    double rk = p->R + ((double)k + 0.5) * p->dx;
-    return (int)round(2.0 * M_PI * rk / p->dx);
+    return (int)round(2.0 * M_PI * ring_radius(p, k) / orc_ghost_ds(p));
 }
 
 /* Particle counts of the tank of reading R9. */
@@ -225,7 +233,7 @@ int orc_tank_build(const orc_params* p, double* xf, double* gB)
             }
     n = 0;
     for (int k = 0; k < p->n_rings; ++k) {
-        double rk = p->R + ((double)k + 0.5) * p->dx;
+        double rk = ring_radius(p, k);
         int Nk = ring_count(p, k);
         for (int j = 0; j < Nk; ++j) {
             double phi = 2.0 * M_PI * (double)j / (double)Nk;
@@ -625,7 +633,8 @@ int orc_run(const orc_params* p, int nf, double* x, double* v, int ng, const dou
 
 /*
  * Neighbour-grid convention: square cells of side s = 2h (1 + 1/1024),
- * half-width W = R + (n_rings + 1) dx + 2 s around an FP64 anchor point,
+ * half-width W = R + (n_rings + 1) max(dx, s_g) + 2 s around an FP64 anchor
+ * point (s_g the ghost spacing),
  * G = ceil(2W / s) cells per side.  A position x (FP32) falls in column
  *   c = floor( fl32( fl32(x - o) * fl32(1/s) ) ),  o = fl32(anchor - W),
  * clamped to [0, G-1]; the key is row * G + column.
@@ -633,7 +642,7 @@ int orc_run(const orc_params* p, int nf, double* x, double* v, int ng, const dou
 int orc_grid_dims(const orc_params* p, double* cell, double* half_width, int32_t* G)
 {
     double s = 2.0 * orc_h(p) * (1.0 + 1.0 / 1024.0);
-    double W = p->R + ((double)p->n_rings + 1.0) * p->dx + 2.0 * s;
+    double W = p->R + ((double)p->n_rings + 1.0) * fmax(p->dx, orc_ghost_ds(p)) + 2.0 * s;
     *cell = s;
     *half_width = W;
     *G = (int32_t)ceil(2.0 * W / s);

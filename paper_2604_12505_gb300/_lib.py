@@ -43,6 +43,7 @@ class SphParams(C.Structure):
         ("gamma1", C.c_double), ("eps", C.c_double), ("m_body", C.c_double), ("J_body", C.c_double),
         ("dt", C.c_double), ("grav_x", C.c_double), ("grav_y", C.c_double), ("sigma_cubic", C.c_double),
         ("ghost_pressure_sign", C.c_double), ("n_rings", C.c_int32), ("outer_every", C.c_int32),
+        ("ghost_spacing", C.c_double),
     ]
 
 
@@ -79,6 +80,7 @@ def _declare(L):
         "sph_vjp": ([vp, vp, i32, vp, vp, vp, vp, vp, vp, i32, vp], C.c_int),
         "sph_time_kernels": ([vp, i32, dp, vp], C.c_int),
         "sph_run_batch": ([P, i32, vp, i32, C.POINTER(SphCtrl), vp, ip, vp], C.c_int),
+        "sph_gamma1_estimate": ([P, dp], C.c_int),
         "sph_density_noalloc": ([P, vp, i32, vp, i32, dp, vp, vp], C.c_int),
         "lpv_create": ([vp, C.POINTER(vp)], C.c_int),
         "lpv_destroy": ([vp], C.c_int),

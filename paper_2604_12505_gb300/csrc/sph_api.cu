@@ -72,6 +72,9 @@ int validate(const sph_params& p)
     return SPH_OK;
 }
 
+// Spacing of the ghosts along a ring and between rings.
+double ghost_ds(const sph_params& p) { return (p.ghost_spacing > 0.0 ? p.ghost_spacing : 1.0) * p.dx; }
+
 // Fluid lattice and ghost rings of one tank (geometry stated on sph_params).
 void build_tank(TankHost& t)
 {
@@ -86,9 +89,10 @@ void build_tank(TankHost& t)
                 t.xf.push_back(y);
             }
         }
+    const double sg = ghost_ds(p);
     for (int k = 0; k < p.n_rings; ++k) {
-        const double rk = p.R + ((double)k + 0.5) * p.dx;
-        const int nk = (int)std::round(2.0 * kPi * rk / p.dx);
+        const double rk = p.R + ((double)k + 0.5) * sg;
+        const int nk = (int)std::round(2.0 * kPi * rk / sg);
         for (int j = 0; j < nk; ++j) {
             const double phi = 2.0 * kPi * (double)j / (double)nk;
             t.gB.push_back(rk * std::cos(phi));
@@ -99,7 +103,7 @@ void build_tank(TankHost& t)
     t.n_g = (int)t.gB.size() / 2;
     t.h = p.h_over_dx * p.dx;
     t.cell = 2.0 * t.h * (1.0 + 1.0 / 1024.0);
-    t.W = p.R + ((double)p.n_rings + 1.0) * p.dx + 2.0 * t.cell;
+    t.W = p.R + ((double)p.n_rings + 1.0) * std::max(p.dx, sg) + 2.0 * t.cell;
     t.G = (int)std::ceil(2.0 * t.W / t.cell);
 }
 
@@ -962,6 +966,58 @@ int sph_run_batch(const sph_params* p, int32_t B, const double* u_profiles, int3
     if (rc == SPH_OK) rc = sph_check(s, nullptr, 0, stream);
     sph_destroy(s);
     return rc;
+}
+
+// Eq. 15 for the reference wall of the boundary sketch.  The lattice sums are
+// taken point by point; the ghost sum, averaged over the offset of the ghost
+// rows against the lattice, is the line integral (1 / s_g) \int W dx of each
+// row (Simpson's rule on each polynomial piece of W along the row).
+int sph_gamma1_estimate(const sph_params* p, double* gamma1)
+{
+    if (!p || !gamma1) return fail(SPH_E_INVAL, "sph_gamma1_estimate: NULL pointer");
+    if (!(p->dx > 0) || !(p->h_over_dx > 0) || p->n_rings < 1)
+        return fail(SPH_E_INVAL, "sph_gamma1_estimate: invalid sph_params");
+    const double dx = p->dx, h = p->h_over_dx * p->dx, sg = ghost_ds(*p);
+    const double sigma = p->sigma_cubic > 0.0 ? p->sigma_cubic : 5.0 / (14.0 * kPi);
+    auto W = [&](double r) {  // Eq. 22 with the normalised constant
+        const double q = r / h;
+        if (q >= 2.0) return 0.0;
+        double f = (2.0 - q) * (2.0 - q) * (2.0 - q);
+        if (q < 1.0) f -= 4.0 * (1.0 - q) * (1.0 - q) * (1.0 - q);
+        return sigma / (h * h) * f;
+    };
+    const int n = (int)std::ceil(2.0 * h / dx) + 1;
+    double lattice = 0.0, fluid = 0.0;
+    for (int b = -n; b <= n; ++b)
+        for (int a = -n; a <= n; ++a) {
+            const double w = W(dx * std::sqrt((double)(a * a + b * b)));
+            lattice += w;
+            if (b >= 0) fluid += w;
+        }
+    auto simpson = [&](double d, double x0, double x1) {  // \int_{x0}^{x1} W(sqrt(x^2 + d^2)) dx
+        const int m = 4096;
+        const double hx = (x1 - x0) / m;
+        double acc = W(std::hypot(x0, d)) + W(std::hypot(x1, d));
+        for (int i = 1; i < m; ++i) acc += (i & 1 ? 4.0 : 2.0) * W(std::hypot(x0 + i * hx, d));
+        return acc * hx / 3.0;
+    };
+    double ghost = 0.0;
+    for (int k = 0; k < p->n_rings; ++k) {
+        const double d = 0.5 * dx + ((double)k + 0.5) * sg;  // depth of ghost row k below particle i
+        if (d >= 2.0 * h) continue;
+        const double x2 = std::sqrt(4.0 * h * h - d * d);
+        double row;
+        if (d < h) {
+            const double x1 = std::sqrt(h * h - d * d);
+            row = simpson(d, 0.0, x1) + simpson(d, x1, x2);
+        } else {
+            row = simpson(d, 0.0, x2);
+        }
+        ghost += 2.0 * row / sg;
+    }
+    if (!(ghost > 0.0)) return fail(SPH_E_INVAL, "sph_gamma1_estimate: no ghost row within the support");
+    *gamma1 = (lattice - fluid) / ghost;
+    return SPH_OK;
 }
 
 }  // extern "C"

@@ -15,6 +15,7 @@
 // call from two threads) race on it and must not be issued.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 
@@ -154,7 +155,8 @@ extern "C" int sph_density_noalloc(const sph_params* p, const float* xv, int32_t
         return set_last_error(SPH_E_UNSUPPORTED, "sph_density_noalloc: more than 2^30 particles");
     const double h = p->h_over_dx * p->dx;
     const double cell = 2.0 * h * (1.0 + 1.0 / 1024.0);
-    const double W = p->R + ((double)p->n_rings + 1.0) * p->dx + 2.0 * cell;
+    const double sg = (p->ghost_spacing > 0.0 ? p->ghost_spacing : 1.0) * p->dx;
+    const double W = p->R + ((double)p->n_rings + 1.0) * std::max(p->dx, sg) + 2.0 * cell;
     const int G = (int)std::ceil(2.0 * W / cell);
     if ((long long)G * G > kMaxCells)
         return set_last_error(SPH_E_UNSUPPORTED, "sph_density_noalloc: neighbour grid wider than 256 x 256 cells "

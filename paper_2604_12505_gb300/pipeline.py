@@ -285,7 +285,7 @@ def linearization_study(cfg: dict | None = None, relax: int = 2000, steps: int =
     from .sph import Sim
 
     say = log or (lambda *a: None)
-    cfg = dict(cfg or W.PAPER)
+    cfg = dict(cfg or W.PAPER_RINGS)
     with Sim(cfg) as sim:
         sim.relax(relax, damping=2e-3)
         xv, body = sim.state()
@@ -320,12 +320,125 @@ def linearization_study(cfg: dict | None = None, relax: int = 2000, steps: int =
     return out
 
 
+def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int = 64, jitter: float = 0.25,
+                         seed: int = 0, gammas=None, log=None) -> dict:
+    """The paper's benchmark spacecraft (Section 5.1, Tables 1 and 2) on this
+    GPU, as context for the simulation times the paper reports (Table 3).
+
+    Spawn: the 6 mm lattice with each coordinate moved by U(-jitter, jitter) dx
+    (seeded), then relaxed with the tank held fixed (damping 2e-3 per step):
+    Section 5.1 spawns the particles at random and lets them come to rest.
+    Flight: `seconds` at dt = 1 ms with seeded piecewise forces and torques,
+    the PD attitude law of Eq. 28 sampled every 50 ms tracking random attitude
+    steps.  Run with Table 2's wall (one layer of 0.9 dx ghosts) for each
+    gamma1 in `gammas` (default: Table 2's 0.5, Eq. 15's estimate from
+    ``sph_gamma1_estimate``, and 1.5), and with this repository's wall (three
+    rings at dx, gamma1 = 1.5), each on one tank (the wall time of one
+    sph_step call over the whole flight, and the largest fluid radius over R
+    checked every second, against the outermost ghost ring) and on `batch`
+    copies with their own spawns and inputs stepped together.  The health flags (SPH_FLAG_*)
+    after the relaxation and after each flight are recorded; a gamma1 whose
+    relaxation already lets fluid through the wall is not flown."""
+    from . import workloads as W
+    from .sph import Sim, gamma1_estimate
+
+    say = log or (lambda *a: None)
+    base = dict(W.PAPER)
+    outer, dt = base["outer_every"], base["dt"]
+    Ts = outer * dt
+    K = int(round(seconds / Ts))
+    g15 = gamma1_estimate(base)
+    walls = [dict(base, gamma1=g) for g in gammas] if gammas is not None else \
+        [base, dict(base, gamma1=g15), dict(base, gamma1=1.5), dict(W.PAPER_RINGS)]
+    F, tau, ref = _closed_loop_inputs(batch, K, Ts, seed0=3000 + seed)
+    u = np.concatenate([F, tau[..., None]], axis=2)                       # [batch, K, 3]
+    ctrl = dict(omega=base["ctrl_omega"], xi=base["ctrl_xi"])
+    out = dict(seconds=seconds, steps=K * outer, dt=dt, Ts=Ts, gamma1_eq15=g15, jitter_dx=jitter,
+               paper=dict(profile1_s=9.9093, horizon_s=30.0, hardware="RTX 2000 Ada laptop GPU, JAX (Table 3)"),
+               runs=[])
+
+    def spawn(sim, seeds):
+        xv, body = sim.state()
+        x = xv.cpu().numpy()
+        o = 0
+        for b, n in enumerate(sim.n_fluid):
+            x[o:o + n, :2] += W.uniform_jitter((n, 2), jitter * base["dx"], seed=seeds[b])
+            o += n
+        sim.set_state(x, body)
+        sim.relax(relax, damping=2e-3)
+        flags = sim.check(reset=True, raise_on_error=False)
+        xv, body = sim.state()
+        vmax = float(xv[:, 2:].norm(dim=1).max().item())
+        xv[:, 2:] = 0.0
+        sim.set_state(xv, body)
+        return vmax, flags
+
+    for cfg in walls:
+        run = dict(gamma1=cfg["gamma1"], rings=cfg["n_rings"], ghost_spacing=cfg["ghost_spacing"])
+        with Sim(cfg) as sim:
+            run["particles"], run["ghosts"] = sim.n_fluid[0], sim.n_ghost[0]
+            run["relax_vmax"], run["relax_flags"] = spawn(sim, [seed])
+            if run["relax_flags"]:
+                say("paper scenario", run)
+                out["runs"].append(run)
+                continue
+            rest = sim.state()
+            ui = torch.tensor(np.repeat(u[:1], outer, axis=1), dtype=torch.float64, device="cuda")
+            rf = torch.tensor(ref[:1], dtype=torch.float64, device="cuda")
+            sim.step(10 * outer, u=ui[:, :10 * outer], ctrl=ctrl, theta_ref=rf[:, :10], record=False)  # warm-up
+            sim.set_state(*rest)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            w0 = time.perf_counter()
+            e0.record()
+            sim.step(K * outer, u=ui, ctrl=ctrl, theta_ref=rf)
+            e1.record()
+            torch.cuda.synchronize()
+            run["one_tank_wall_s"] = time.perf_counter() - w0
+            run["one_tank_device_s"] = e0.elapsed_time(e1) * 1e-3
+            run["flight_flags"] = sim.check(reset=True, raise_on_error=False)
+            # the same flight in one-second pieces, for the largest radius
+            sim.set_state(*rest)
+            per = int(round(1.0 / Ts))
+            rmax = 0.0
+            for k0 in range(0, K, per):
+                k1 = min(K, k0 + per)
+                sim.step((k1 - k0) * outer, u=ui[:, k0 * outer:k1 * outer], ctrl=ctrl, theta_ref=rf[:, k0:k1],
+                         record=False)
+                xv, body = sim.state()
+                d = xv[:, :2].double() - body[0, :2]
+                rmax = max(rmax, float(d.norm(dim=1).max().item()))
+            sim.check(reset=True, raise_on_error=False)
+            run["max_radius_over_R"] = rmax / base["R"]
+            run["escaped_past_ghosts"] = bool(rmax > base["R"] + (cfg["n_rings"] - 0.5) * cfg["ghost_spacing"] * base["dx"])
+        with Sim([cfg] * batch) as sim:
+            sim.autotune(steps=10)
+            _, bflags = spawn(sim, [seed + 1 + b for b in range(batch)])
+            ub = torch.tensor(np.repeat(u, outer, axis=1), dtype=torch.float64, device="cuda")
+            rb = torch.tensor(ref, dtype=torch.float64, device="cuda")
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sim.step(K * outer, u=ub, ctrl=ctrl, theta_ref=rb, record=False)
+            e1.record()
+            torch.cuda.synchronize()
+            tb = e0.elapsed_time(e1) * 1e-3
+            run["batch"] = dict(tanks=batch, device_s=tb, flights_per_s=batch / tb, relax_flags=bflags,
+                                flight_flags=sim.check(reset=True, raise_on_error=False))
+        run["speedup_vs_paper_one_tank"] = out["paper"]["profile1_s"] * (seconds / 30.0) / run["one_tank_wall_s"]
+        say("paper scenario", run)
+        out["runs"].append(run)
+    return out
+
+
 if __name__ == "__main__":
     import json
     import sys
 
     if len(sys.argv) > 1 and sys.argv[1] == "linearize":
         print(json.dumps(linearization_study(log=lambda *a: print(*a, file=sys.stderr))))
+    elif len(sys.argv) > 1 and sys.argv[1] == "paper":
+        print(json.dumps(paper_scenario_study(log=lambda *a: print(*a, file=sys.stderr))))
     else:
-        print("usage: python -m paper_2604_12505_gb300.pipeline linearize", file=sys.stderr)
+        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper", file=sys.stderr)
         sys.exit(2)

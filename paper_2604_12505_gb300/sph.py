@@ -272,3 +272,12 @@ def run_batch(params: Sequence[dict], u_profiles, T: int, ctrl: dict | None = No
     check(lib().sph_run_batch(arr, B, _ptr(u), T, None if c is None else C.byref(c), _ptr(y), npart,
                               _stream(stream)), "sph_run_batch")
     return y, list(npart)
+
+
+def gamma1_estimate(params: dict) -> float:
+    """Eq. 15's boundary correcting factor for a representative wall of the
+    tank ``params`` (the library's ``sph_gamma1_estimate``; host-side, no
+    device work)."""
+    g = C.c_double()
+    check(lib().sph_gamma1_estimate(C.byref(make_params(params)), C.byref(g)), "sph_gamma1_estimate")
+    return g.value

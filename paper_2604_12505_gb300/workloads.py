@@ -35,6 +35,7 @@ BASE = dict(
     ctrl_xi=0.7,
     n_rings=3,
     outer_every=10,
+    ghost_spacing=1.0,        # ghosts spaced like the fluid lattice
 )
 
 # Small tank: R = 0.5 m, 50 % fill, dx = 0.02 m (938 fluid + 500 ghosts).
@@ -47,12 +48,16 @@ JVP = dict(BASE, dx=0.005)
 TINY = dict(BASE, R=0.1, dx=0.01)
 # The paper's benchmark spacecraft (Tables 1 and 2): R = 0.2 m at 60 % fill,
 # 6 mm particles, h = 9.42 mm, rho0 = 1017, body 1010.71 kg and
-# 133.84 kg m^2, dt = 1 ms, outputs every 50 ms.  The fluid is this
+# 133.84 kg m^2, dt = 1 ms, outputs every 50 ms, and the wall as one layer of
+# 236 ghosts 5.4 mm long (0.9 dx) with gamma1 = 0.5.  The fluid is this
 # repository's lattice at 6 mm (2,024 particles rather than the paper's 666,
-# which no lattice or packing of 6 mm particles in that tank gives) with three
-# rings of ghosts at 6 mm and gamma1 = 1.5.
+# which no lattice or packing of 6 mm particles in that tank gives).
 PAPER = dict(BASE, R=0.2, fill=0.6, dx=0.006, h_over_dx=9.42 / 6.0, rho0=1017.0, m_body=1010.71, J_body=133.84,
-             dt=1e-3, outer_every=50)
+             dt=1e-3, outer_every=50, n_rings=1, ghost_spacing=0.9, gamma1=0.5)
+# The same spacecraft with this repository's wall: three rings of ghosts at
+# 6 mm and gamma1 = 1.5 (the single layer of Table 2 lets this lattice fluid
+# through the wall).
+PAPER_RINGS = dict(PAPER, n_rings=3, ghost_spacing=1.0, gamma1=1.5)
 
 
 def small_torque_pulse(n_steps: int, dt: float, tau: float = 1.0, t_on: float = 0.05) -> np.ndarray:
@@ -100,6 +105,11 @@ def piecewise_profile(n_samples: int, Ts: float, seed: int, hold=(0.05, 0.5), ta
 def perturbation(shape, scale: float, seed: int) -> np.ndarray:
     """Seeded normal perturbation N(0, scale^2) of the given shape."""
     return np.random.default_rng(seed).normal(0.0, scale, size=shape)
+
+
+def uniform_jitter(shape, half_width: float, seed: int) -> np.ndarray:
+    """Seeded offsets ~ U(-half_width, half_width) of the given shape."""
+    return np.random.default_rng(seed).uniform(-half_width, half_width, size=shape)
 
 
 def unit_directions(n_dir: int, dim: int, seed: int) -> np.ndarray:

@@ -72,3 +72,20 @@ def test_study_on_the_identification_train():
     assert r["inputs"] == "train" and r["dataset"]["trajectories"] == 10
     for name in ("lpv", "lti", "no_fluid"):
         assert all(np.isfinite(v) for v in r[f"closed_loop_{name}"]["nrmse"].values())
+
+
+@pytest.mark.gpu
+def test_paper_scenario_study_short():
+    """The Tables 1-2 spacecraft: one 236-ghost layer, a jittered spawn relaxed
+    to rest, a short PD-controlled flight per gamma1, health flags recorded."""
+    need_gpu()
+    from paper_2604_12505_gb300 import pipeline as PL
+    r = PL.paper_scenario_study(seconds=1.0, relax=1000, batch=2, gammas=[0.5, 1.5])
+    assert r["steps"] == 1000 and [x["gamma1"] for x in r["runs"]] == [0.5, 1.5]
+    assert 0.5 < r["gamma1_eq15"] < 2.0
+    for run in r["runs"]:
+        assert run["particles"] == 2024 and run["ghosts"] == 236
+        assert isinstance(run["relax_flags"], int) and np.isfinite(run["relax_vmax"])
+        if run["relax_flags"] == 0:
+            assert run["one_tank_device_s"] > 0 and 0.5 < run["max_radius_over_R"]
+            assert run["batch"]["tanks"] == 2 and run["batch"]["flights_per_s"] > 0

@@ -33,7 +33,10 @@ def _sim(cfg):
 
 
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("cfg", [W.TINY, W.SMALL, W.JVP])
+SINGLE_RING = dict(W.SMALL, n_rings=1, ghost_spacing=0.9)  # one wall layer of 0.9 dx ghosts (Table 2's form)
+
+
+@pytest.mark.parametrize("cfg", [W.TINY, W.SMALL, W.JVP, W.PAPER, SINGLE_RING])
 def test_tank_builder_matches_oracle(torch_mod, orc, cfg):
     p = orc.params(**cfg)
     x, gB = orc.tank(p)
@@ -50,6 +53,8 @@ def test_tank_builder_matches_oracle(torch_mod, orc, cfg):
     (W.SMALL, 0.0, 0.0, [0.0] * 6),
     (W.SMALL, 0.25, 0.5, [0.013, 0.021, -1.3, 0.2, 0.1, -0.9]),
     (dict(W.SMALL, ghost_pressure_sign=1.0, gamma1=1.0), 0.2, 0.4, [0.0, 0.0, 0.3, 0.0, 0.0, 0.2]),
+    (SINGLE_RING, 0.25, 0.4, [0.01, -0.02, 0.8, 0.1, 0.2, -0.6]),
+    (W.PAPER, 0.2, 0.3, [0.002, -0.001, 0.2, 0.05, 0.02, 0.4]),
 ])
 def test_one_step_eval_parity(torch_mod, orc, cfg, pos, vel, body):
     torch = torch_mod
@@ -85,9 +90,9 @@ def test_one_step_eval_parity(torch_mod, orc, cfg, pos, vel, body):
     np.testing.assert_array_equal(nbr[:, 2], nfg1)
 
 
-@pytest.mark.parametrize("ctrl", [False, True])
-def test_trajectory_parity_200_steps(torch_mod, orc, ctrl):
-    cfg = dict(W.SMALL, outer_every=5)
+@pytest.mark.parametrize("ctrl,base", [(False, W.SMALL), (True, W.SMALL), (False, SINGLE_RING)])
+def test_trajectory_parity_200_steps(torch_mod, orc, ctrl, base):
+    cfg = dict(base, outer_every=5)
     n = 200
     u = W.small_torque_pulse(n, cfg["dt"], tau=2000.0, t_on=0.005)
     u[:, 0] = 300.0
@@ -274,3 +279,11 @@ def test_relaxation_parity(torch_mod, orc):
     disp = np.linalg.norm(xr - x, axis=1).max()
     assert np.linalg.norm(xg[:, :2] - xr, axis=1).max() <= 1e-3 * disp
     assert normwise(xg[:, 2:], vr) <= 1e-3
+
+
+@pytest.mark.parametrize("cfg", [W.LARGE, W.PAPER, SINGLE_RING, dict(W.SMALL, h_over_dx=2.0, n_rings=2, ghost_spacing=1.2)])
+def test_gamma1_estimate_matches_oracle(torch_mod, orc, cfg):
+    """Eq. 15's estimate: the library integrates each ghost row along the
+    wall, the oracle averages the row over its offsets."""
+    from paper_2604_12505_gb300.sph import gamma1_estimate
+    assert gamma1_estimate(cfg) == pytest.approx(orc.gamma1_estimate(orc.params(**cfg)), rel=1e-9)
