@@ -82,6 +82,17 @@ def _declare(L):
         "sph_run_batch": ([P, i32, vp, i32, C.POINTER(SphCtrl), vp, ip, vp], C.c_int),
         "sph_gamma1_estimate": ([P, dp], C.c_int),
         "sph_density_noalloc": ([P, vp, i32, vp, i32, dp, vp, vp], C.c_int),
+        "slpv_n_params": ([i32, ip], C.c_int),
+        "slpv_create": ([vp, C.POINTER(vp)], C.c_int),
+        "slpv_destroy": ([vp], C.c_int),
+        "slpv_set_params": ([vp, vp, vp], C.c_int),
+        "slpv_get_params": ([vp, vp, vp], C.c_int),
+        "slpv_normalize": ([vp, vp, vp, i32, i32, vp], C.c_int),
+        "slpv_loss_grad": ([vp, vp, vp, i32, i32, i32, vp, vp, vp], C.c_int),
+        "slpv_train": ([vp, vp, vp, i32, i32, i32, C.c_float, i32, vp, vp], C.c_int),
+        "slpv_predict": ([vp, vp, i32, i32, C.c_double, vp, vp, vp], C.c_int),
+        "slpv_simulate": ([vp, i32, i32, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double, vp, vp],
+                          C.c_int),
         "lpv_create": ([vp, C.POINTER(vp)], C.c_int),
         "lpv_destroy": ([vp], C.c_int),
         "lpv_set_params": ([vp, vp, vp], C.c_int),

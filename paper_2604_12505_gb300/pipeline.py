@@ -431,6 +431,113 @@ def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int 
     return out
 
 
+def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int = 2200, relax: int = 20_000,
+                             lti_iters: int = 1000, lti_lr: float = 1e-2, adam_iters: int = 2000, lr: float = 1e-3,
+                             restarts: int = 8, cl_samples: int = 600, n_sims: int = 65_536, nx: int = 4,
+                             sigma2: float = 1e-4, seed: int = 0, log=None) -> dict:
+    """The paper's identification study (Section 5.3) on its spacecraft.
+
+    1. D_N: n_train copies of the Tables 1-2 spacecraft (three ghost rings,
+       `workloads.PAPER_RINGS`), relaxed, each driven open loop by its own
+       identification train (pulses, then a random-phase multisine on
+       [0, 2) Hz at 0.05 Hz; 2200 samples at T_s = 0.05 s) and sampled every
+       T_s: inputs u = [F_x, F_y, tau], outputs the body velocities
+       [rdot_x, rdot_y, thetadot] (the velocity-level reformulation).
+    2. The self-scheduled LPV model (n_x = 4, n_p = 1, eta a 2 x 4 tanh
+       network, D = 0): an LTI stage (M_0 only, from a stable start) stands
+       in for the ssest fit; then `restarts` LPV fits from it with random
+       M_1 and Xavier network weights, Adam, the lowest training loss kept.
+    3. Validation as in Table 3: n_val closed-loop manoeuvres of
+       cl_samples * T_s seconds (the PD law of Eq. 28 tracking random attitude
+       steps, piecewise forces and torques) flown by the SPH simulator and by
+       the augmented surrogates (LTI and LPV) with the same inputs; BFR per
+       channel (r_x, r_y, theta, rdot_x, rdot_y, thetadot).
+    4. Throughput: n_sims surrogate closed loops at once, against the
+       simulator's flights per second on the validation batch."""
+    from . import workloads as W
+    from .slpv import VelocityModel, initial_theta
+
+    say = log or (lambda *a: None)
+    cfg = dict(W.PAPER_RINGS)
+    Ts = cfg["dt"] * cfg["outer_every"]
+    out = dict(Ts=Ts, id_samples=id_samples, n_train=n_train, n_val=n_val, nx=nx)
+    t0 = time.perf_counter()
+    tanks = Tanks([cfg] * n_train, relax_steps=relax)
+    u_id = np.stack([W.identification_train(id_samples, Ts, seed=5000 + seed * 1000 + b) for b in range(n_train)])
+    ys, sec = tanks.run(u_id)
+    tanks.close()
+    out["dataset"] = dict(sph_device_s=sec, wall_s=time.perf_counter() - t0)
+    u = torch.tensor(u_id, dtype=torch.float32, device="cuda")
+    y = torch.tensor(ys[:, :, 3:6], dtype=torch.float32, device="cuda")
+    say("velocity surrogate: data", out["dataset"])
+
+    m = VelocityModel(nx=nx, sigma2=sigma2)
+    m.normalize(u, y)
+    _, sc = m.get_params()
+    t1 = time.perf_counter()
+    m.set_params(initial_theta(nx, seed=seed), sc)
+    h = m.train(u, y, lti_iters, lti_lr, lti_only=True).cpu().numpy()
+    th_lti, _ = m.get_params()
+    fits = dict(lti=dict(loss=float(h[-1]), seconds=time.perf_counter() - t1))
+    best = None
+    for r in range(restarts):
+        t2 = time.perf_counter()
+        m.set_params(initial_theta(nx, seed=seed * 100 + r + 1, base=th_lti), sc)
+        h = m.train(u, y, adam_iters, lr).cpu().numpy()
+        loss = float(m.loss_grad(u, y, grad=False)[0].item())
+        say("velocity surrogate: restart", r, loss, time.perf_counter() - t2)
+        if np.isfinite(loss) and (best is None or loss < best[0]):
+            best = (loss, m.get_params()[0])
+    fits["lpv"] = dict(loss=best[0] if best else float("nan"), seconds=time.perf_counter() - t1 - fits["lti"]["seconds"],
+                       restarts=restarts, adam_iters=adam_iters)
+    out["fit"] = fits
+    # training-set BFR of the free run (velocities)
+    yv = ys[:, :, 3:6]
+
+    def bfr_of(model_theta):
+        m.set_params(model_theta, sc)
+        vh, _ = m.predict(u, Ts)
+        vh = vh.cpu().numpy()
+        return [float(100.0 * (1.0 - np.mean([nrmse(yv[b, :, c], vh[b, :, c]) for b in range(n_train)])))
+                for c in range(3)]
+
+    out["train_bfr_velocity"] = dict(lti=bfr_of(th_lti), lpv=bfr_of(best[1]) if best else None)
+
+    # closed-loop validation (Table 3 style)
+    K = cl_samples
+    F, tau, ref = _closed_loop_inputs(n_val, K, Ts, seed0=7000 + seed)
+    ctrl = dict(omega=cfg["ctrl_omega"], xi=cfg["ctrl_xi"])
+    val = Tanks([cfg] * n_val, relax_steps=relax)
+    ysph, t_sph = val.run(np.concatenate([F, tau[..., None]], axis=2), ctrl=ctrl, theta_ref=ref)
+    val.close()
+    ref_traj = ysph[:, :, :6]
+    chans = ("r_x", "r_y", "theta", "rdot_x", "rdot_y", "thetadot")
+    out["validation"] = dict(seconds=K * Ts, sph_device_s=t_sph, sph_flights_per_s=n_val / t_sph)
+    for name, th in (("lti", th_lti), ("lpv", best[1] if best else th_lti)):
+        m.set_params(th, sc)
+        sim = m.simulate(F, tau, ref, Ts, cfg["J_body"], ctrl["omega"], ctrl["xi"]).cpu().numpy()
+        bfr = {c: float(100.0 * (1.0 - np.mean([nrmse(ref_traj[b, :, i], sim[b, :, i]) for b in range(n_val)])))
+               for i, c in enumerate(chans)}
+        out["validation"][name] = bfr
+        say("velocity surrogate: closed-loop BFR", name, bfr)
+    # throughput of the surrogate closed loop
+    Fb = torch.tensor(np.tile(F, (n_sims // n_val + 1, 1, 1))[:n_sims], device="cuda")
+    tb = torch.tensor(np.tile(tau, (n_sims // n_val + 1, 1))[:n_sims], device="cuda")
+    rb = torch.tensor(np.tile(ref, (n_sims // n_val + 1, 1))[:n_sims], device="cuda")
+    m.simulate(Fb[:64], tb[:64], rb[:64], Ts, cfg["J_body"], ctrl["omega"], ctrl["xi"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    m.simulate(Fb, tb, rb, Ts, cfg["J_body"], ctrl["omega"], ctrl["xi"])
+    e1.record()
+    torch.cuda.synchronize()
+    t_sur = e0.elapsed_time(e1) * 1e-3
+    out["throughput"] = dict(surrogate_sims=n_sims, samples=K, surrogate_s=t_sur, surrogate_sims_per_s=n_sims / t_sur,
+                             sph_flights_per_s=n_val / t_sph, speedup=(n_sims / t_sur) / (n_val / t_sph))
+    m.close()
+    return out
+
+
 if __name__ == "__main__":
     import json
     import sys
@@ -439,6 +546,8 @@ if __name__ == "__main__":
         print(json.dumps(linearization_study(log=lambda *a: print(*a, file=sys.stderr))))
     elif len(sys.argv) > 1 and sys.argv[1] == "paper":
         print(json.dumps(paper_scenario_study(log=lambda *a: print(*a, file=sys.stderr))))
+    elif len(sys.argv) > 1 and sys.argv[1] == "velocity":
+        print(json.dumps(velocity_surrogate_study(log=lambda *a: print(*a, file=sys.stderr))))
     else:
-        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper", file=sys.stderr)
+        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper|velocity", file=sys.stderr)
         sys.exit(2)

@@ -89,3 +89,19 @@ def test_paper_scenario_study_short():
         if run["relax_flags"] == 0:
             assert run["one_tank_device_s"] > 0 and 0.5 < run["max_radius_over_R"]
             assert run["batch"]["tanks"] == 2 and run["batch"]["flights_per_s"] > 0
+
+
+@pytest.mark.gpu
+def test_velocity_surrogate_study_short():
+    """The paper's identification study at toy sizes: data from the spacecraft
+    under identification trains, LTI and LPV fits, closed-loop BFR."""
+    need_gpu()
+    from paper_2604_12505_gb300 import pipeline as PL
+    r = PL.velocity_surrogate_study(n_train=3, n_val=2, id_samples=200, relax=1000, lti_iters=30, adam_iters=30,
+                                    restarts=2, cl_samples=100, n_sims=1024)
+    assert r["fit"]["lti"]["loss"] > 0 and np.isfinite(r["fit"]["lpv"]["loss"])
+    assert len(r["train_bfr_velocity"]["lpv"]) == 3
+    for name in ("lti", "lpv"):
+        assert set(r["validation"][name]) == {"r_x", "r_y", "theta", "rdot_x", "rdot_y", "thetadot"}
+        assert all(np.isfinite(v) for v in r["validation"][name].values())
+    assert r["throughput"]["surrogate_sims"] == 1024 and r["throughput"]["speedup"] > 1.0
