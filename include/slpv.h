@@ -57,6 +57,17 @@ int slpv_get_params(const slpv_model* m, float* theta, float* scales);
 int slpv_normalize(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, void* stream);
 
 /*
+ * Least-squares LTI start of M_0, in place of the ssest fit of Section
+ * 5.3.2: the first-order ARX model y_{k+1} = A1 y_k + B1 u_k fitted in FP64
+ * by the normal equations (ridge 1e-12 tr(G)/6) over all samples of u, y
+ * [n_traj, T, 3] divided by the stored scales, realised with the velocities
+ * as the first three states: A_0 = [[A1, 0], [0, 0]], B_0 = [[B1], [0]],
+ * C_0 = [I, 0]; M_1 and the network set to zero.  Needs nx >= 3.  Blocks.
+ * SPH_E_DIVERGED: singular normal equations.
+ */
+int slpv_init_ls(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, void* stream);
+
+/*
  * Free-run loss of Eq. 27 (x_0 = 0, so the sigma_x term vanishes):
  *   J = mean over the n_traj * T samples of ||y_k / s_y - y_hat_k||^2 + sigma2/2 ||theta||^2
  * and its gradient by backpropagation through time, through the state
@@ -76,6 +87,18 @@ int slpv_loss_grad(slpv_model* m, const float* u, const float* y, int32_t n_traj
  * lti_only as in slpv_loss_grad.
  */
 int slpv_train(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t iters, float lr,
+               int32_t lti_only, double* loss_hist, void* stream);
+
+/*
+ * L-BFGS refinement after Adam (Section 5.3.2): up to iters iterations from
+ * the current theta; the two-loop recursion over the last 10 curvature pairs
+ * runs in FP64 on the device, the step is 1 (0.01 / |g| after a reset)
+ * halved until Armijo's condition (1e-4) holds.  Stops early at a point
+ * without descent.  loss_hist: HOST double [iters] or NULL (the accepted
+ * loss per iteration, the last one repeated after a stop).  Blocks.
+ * SPH_E_DIVERGED: the loss at the start is not finite.
+ */
+int slpv_lbfgs(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t iters,
                int32_t lti_only, double* loss_hist, void* stream);
 
 /*

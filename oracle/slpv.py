@@ -180,3 +180,23 @@ def closed_loop(theta, nx, scales, F, tau, theta_ref, Ts, pd):
         x = o[:nx]
         un_prev = un
     return out
+
+
+def ls_start(U, Y, nx):
+    """Least-squares LTI start of M_0 (stands in for the ssest fit of Section
+    5.3.2): the first-order ARX model y_{k+1} = A1 y_k + B1 u_k fitted by the
+    normal equations over all samples of all trajectories (normalised data),
+    realised with the velocities as the first three states: A_0 = [[A1, 0],
+    [0, 0]], B_0 = [[B1], [0]], C_0 = [I, 0]; M_1 and the network zero."""
+    ny, nu = Y[0].shape[1], U[0].shape[1]
+    Phi = np.concatenate([np.concatenate([y[:-1], u[:-1]], axis=1) for u, y in zip(U, Y)])
+    Tgt = np.concatenate([y[1:] for y in Y])
+    G = Phi.T @ Phi
+    R = Phi.T @ Tgt
+    Th = np.linalg.solve(G + 1e-12 * np.trace(G) / G.shape[0] * np.eye(G.shape[0]), R)   # [ny+nu, ny]
+    A1, B1 = Th[:ny].T, Th[ny:].T
+    P = unpack(np.zeros(sum(sizes(nx, nu, ny))), nx, nu, ny)
+    P["M0"][:ny, :ny] = A1
+    P["M0"][:ny, nx:] = B1
+    P["M0"][nx:, :ny] = np.eye(ny)
+    return pack(P)

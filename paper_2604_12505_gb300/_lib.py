@@ -90,6 +90,8 @@ def _declare(L):
         "slpv_normalize": ([vp, vp, vp, i32, i32, vp], C.c_int),
         "slpv_loss_grad": ([vp, vp, vp, i32, i32, i32, vp, vp, vp], C.c_int),
         "slpv_train": ([vp, vp, vp, i32, i32, i32, C.c_float, i32, vp, vp], C.c_int),
+        "slpv_lbfgs": ([vp, vp, vp, i32, i32, i32, i32, vp, vp], C.c_int),
+        "slpv_init_ls": ([vp, vp, vp, i32, i32, vp], C.c_int),
         "slpv_predict": ([vp, vp, i32, i32, C.c_double, vp, vp, vp], C.c_int),
         "slpv_simulate": ([vp, i32, i32, vp, vp, vp, C.c_double, C.c_double, C.c_double, C.c_double, vp, vp],
                           C.c_int),

@@ -14,6 +14,7 @@
 // are deterministic.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -316,6 +317,115 @@ __global__ void adam_kernel(AdamDev A, const float* __restrict__ grad, const dou
 }
 
 // ---------------------------------------------------------------------------
+// L-BFGS (one block, one thread per entry of theta; FP64 state)
+// ---------------------------------------------------------------------------
+constexpr int kLM = 10;   // curvature pairs kept
+constexpr int kLT = 320;  // threads: at least n_theta (315 for nx = 8)
+
+struct LbDev {
+    double *W, *g, *d, *S, *Y, *rho, *gd;
+    int* count;  // [0] pairs held, [1] next slot
+    int N;
+};
+
+__device__ double block_dot(double v, double* red)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < kLT / 32; ++w) t += red[w];
+    return t;  // every thread, fixed order
+}
+
+// W = theta, g = grad (zero on fixed entries), no pairs.
+__global__ void lb_init_kernel(const float* __restrict__ th, const float* __restrict__ grad, LbDev L)
+{
+    const int i = threadIdx.x;
+    L.W[i] = i < L.N ? (double)th[i] : 0.0;
+    L.g[i] = i < L.N ? (double)grad[i] : 0.0;
+    if (i == 0) L.count[0] = L.count[1] = 0;
+}
+
+// d = -H g by the two-loop recursion (newest pair first), H_0 = (s.y / y.y) I
+// of the newest pair; d = -g (history cleared) when that is no descent
+// direction.  gd[0] = g.d, gd[1] = g.g.
+__global__ void lb_dir_kernel(LbDev L)
+{
+    __shared__ double red[kLT / 32];
+    __shared__ double alpha[kLM];
+    const int i = threadIdx.x;
+    const int n = L.count[0], next = L.count[1];
+    double q = L.g[i];
+    for (int k = 0; k < n; ++k) {
+        const int j = (next - 1 - k + kLM) % kLM;
+        const double a = L.rho[j] * block_dot(L.S[j * kLT + i] * q, red);
+        if (i == 0) alpha[j] = a;
+        q -= a * L.Y[j * kLT + i];
+    }
+    double gamma = 1.0;
+    if (n > 0) {
+        const int j = (next - 1 + kLM) % kLM;
+        const double yy = block_dot(L.Y[j * kLT + i] * L.Y[j * kLT + i], red);
+        gamma = yy > 0.0 ? 1.0 / (L.rho[j] * yy) : 1.0;
+    }
+    __syncthreads();
+    double r = gamma * q;
+    for (int k = n - 1; k >= 0; --k) {
+        const int j = (next - 1 - k + kLM) % kLM;
+        const double b = L.rho[j] * block_dot(L.Y[j * kLT + i] * r, red);
+        r += L.S[j * kLT + i] * (alpha[j] - b);
+    }
+    const double gi = L.g[i];
+    const double gd = -block_dot(gi * r, red);
+    const double gg = block_dot(gi * gi, red);
+    if (gd < 0.0) {
+        L.d[i] = -r;
+        if (i == 0) L.gd[0] = gd;
+    } else {
+        L.d[i] = -gi;
+        if (i == 0) {
+            L.gd[0] = -gg;
+            L.count[0] = 0;
+        }
+    }
+    if (i == 0) L.gd[1] = gg;
+}
+
+// theta = W + step d (the trial point; fixed entries have d = 0).
+__global__ void lb_try_kernel(float* __restrict__ th, LbDev L, double step)
+{
+    const int i = threadIdx.x;
+    if (i < L.N) th[i] = (float)(L.W[i] + step * L.d[i]);
+}
+
+// Accepts the trial point: s = step d, y = g_new - g, stored when s.y > 0.
+__global__ void lb_accept_kernel(const float* __restrict__ grad, LbDev L, double step)
+{
+    __shared__ double red[kLT / 32];
+    const int i = threadIdx.x;
+    const double gn = i < L.N ? (double)grad[i] : 0.0;
+    const double s = step * L.d[i], y = gn - L.g[i];
+    const double sy = block_dot(s * y, red);
+    const double yy = block_dot(y * y, red);
+    const int next = L.count[1];
+    __syncthreads();
+    if (sy > 1e-12 * yy && sy > 0.0) {
+        L.S[next * kLT + i] = s;
+        L.Y[next * kLT + i] = y;
+        if (i == 0) {
+            L.rho[next] = 1.0 / sy;
+            L.count[0] = min(L.count[0] + 1, kLM);
+            L.count[1] = (next + 1) % kLM;
+        }
+    }
+    L.W[i] += s;
+    L.g[i] = gn;
+}
+
+// ---------------------------------------------------------------------------
 // Free run of the augmented model (velocities and positions, physical units)
 // ---------------------------------------------------------------------------
 template <int NX>
@@ -454,6 +564,113 @@ __global__ void stats_final_kernel(const double* __restrict__ part, int nblk, lo
     scales[c] = (float)sqrt(t / (double)n);
 }
 
+// ---------------------------------------------------------------------------
+// Least-squares LTI start: y_{k+1} = A1 y_k + B1 u_k over all samples
+// (normalised), normal equations G = sum phi phi^T, R = sum phi t^T with
+// phi = [y_k; u_k], t = y_{k+1}; per-block FP64 partials, fixed-order sums.
+// ---------------------------------------------------------------------------
+constexpr int kLsThreads = 128;
+constexpr int kLsVals = 36 + 18;  // G (6 x 6) and R (6 x 3)
+
+__global__ void ls_gram_kernel(const float* __restrict__ u, const float* __restrict__ y,
+                               const float* __restrict__ scales, int n_traj, int T, double* __restrict__ part)
+{
+    __shared__ double red[kLsThreads];
+    double acc[kLsVals];
+#pragma unroll
+    for (int i = 0; i < kLsVals; ++i) acc[i] = 0.0;
+    const long long n = (long long)n_traj * (T - 1);
+    for (long long s = blockIdx.x * (long long)kLsThreads + threadIdx.x; s < n; s += (long long)gridDim.x * kLsThreads) {
+        const int tr = (int)(s / (T - 1)), k = (int)(s % (T - 1));
+        const size_t r0 = ((size_t)tr * T + k) * 3, r1 = r0 + 3;
+        double ph[6], t[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            ph[c] = (double)y[r0 + c] / (double)scales[3 + c];
+            ph[3 + c] = (double)u[r0 + c] / (double)scales[c];
+            t[c] = (double)y[r1 + c] / (double)scales[3 + c];
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+#pragma unroll
+            for (int j = 0; j < 6; ++j) acc[i * 6 + j] = fma(ph[i], ph[j], acc[i * 6 + j]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[36 + i * 3 + c] = fma(ph[i], t[c], acc[36 + i * 3 + c]);
+        }
+    }
+    for (int v = 0; v < kLsVals; ++v) {  // block sums in thread order
+        red[threadIdx.x] = acc[v];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int i = 0; i < kLsThreads; ++i) t += red[i];
+            part[blockIdx.x * kLsVals + v] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// Sums the partials, solves (G + 1e-12 tr(G)/6 I) Theta = R by Cholesky and
+// writes theta: A_0 = [[A1, 0], [0, 0]], B_0 = [[B1], [0]], C_0 = [I, 0], the
+// rest zero.
+template <int NX>
+__global__ void ls_solve_kernel(const double* __restrict__ part, int nblk, float* __restrict__ theta,
+                                int* __restrict__ status)
+{
+    using Q = Lay<NX>;
+    for (int i = threadIdx.x; i < Q::N; i += blockDim.x) theta[i] = 0.f;
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    double G[36], R[18];
+    for (int v = 0; v < kLsVals; ++v) {
+        double t = 0.0;
+        for (int b = 0; b < nblk; ++b) t += part[b * kLsVals + v];
+        if (v < 36) G[v] = t; else R[v - 36] = t;
+    }
+    double tr = 0.0;
+    for (int i = 0; i < 6; ++i) tr += G[i * 6 + i];
+    for (int i = 0; i < 6; ++i) G[i * 6 + i] += 1e-12 * tr / 6.0;
+    // Cholesky G = L L^T in place (lower triangle)
+    for (int j = 0; j < 6; ++j) {
+        double d = G[j * 6 + j];
+        for (int k = 0; k < j; ++k) d -= G[j * 6 + k] * G[j * 6 + k];
+        if (!(d > 0.0)) {
+            *status = 1;
+            return;
+        }
+        d = sqrt(d);
+        G[j * 6 + j] = d;
+        for (int i = j + 1; i < 6; ++i) {
+            double s = G[i * 6 + j];
+            for (int k = 0; k < j; ++k) s -= G[i * 6 + k] * G[j * 6 + k];
+            G[i * 6 + j] = s / d;
+        }
+    }
+    double X[18];
+    for (int c = 0; c < 3; ++c) {  // L z = r, L^T x = z
+        double z[6];
+        for (int i = 0; i < 6; ++i) {
+            double s = R[i * 3 + c];
+            for (int k = 0; k < i; ++k) s -= G[i * 6 + k] * z[k];
+            z[i] = s / G[i * 6 + i];
+        }
+        for (int i = 5; i >= 0; --i) {
+            double s = z[i];
+            for (int k = i + 1; k < 6; ++k) s -= G[k * 6 + i] * X[k * 3 + c];
+            X[i * 3 + c] = s / G[i * 6 + i];
+        }
+    }
+    // y_{k+1}[c] = sum_i X[i][c] phi[i]: A1[c][j] = X[j][c], B1[c][j] = X[3 + j][c]
+    for (int c = 0; c < 3; ++c) {
+        for (int j = 0; j < 3; ++j) {
+            theta[Q::M0 + c * Q::NZ + j] = (float)X[j * 3 + c];
+            theta[Q::M0 + c * Q::NZ + NX + j] = (float)X[(3 + j) * 3 + c];
+        }
+        theta[Q::M0 + (NX + c) * Q::NZ + c] = 1.0f;
+    }
+    *status = 0;
+}
+
 }  // namespace slpvk
 
 using namespace slpvk;
@@ -470,6 +687,8 @@ struct slpv_model {
     float* xh = nullptr;
     size_t xh_cap = 0;
     double* spart = nullptr;
+    double* lb = nullptr;  // L-BFGS state, allocated on first use
+    int* lb_count = nullptr;
 };
 
 namespace {
@@ -581,6 +800,8 @@ int slpv_destroy(slpv_model* m)
     cudaFree(m->part);
     cudaFree(m->xh);
     cudaFree(m->spart);
+    cudaFree(m->lb);
+    cudaFree(m->lb_count);
     delete m;
     return SPH_OK;
 }
@@ -697,6 +918,114 @@ int slpv_train(slpv_model* m, const float* u, const float* y, int32_t n_traj, in
     }
     // end on the last accepted iterate
     SCK(cudaMemcpyAsync(m->th, m->thb, nb, cudaMemcpyDeviceToDevice, st));
+    return SPH_OK;
+}
+
+int slpv_lbfgs(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t iters,
+               int32_t lti_only, double* loss_hist, void* stream)
+{
+    int rc = check_data(m, u, n_traj, T);
+    if (rc) return rc;
+    if (!y || iters < 0) return inval("slpv_lbfgs: NULL y or iters < 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!m->lb) {
+        const size_t n = (size_t)kLT * (3 + 2 * kLM) + kLM + 2;
+        if (cudaMalloc(&m->lb, n * sizeof(double)) != cudaSuccess || cudaMalloc(&m->lb_count, 2 * sizeof(int)) != cudaSuccess)
+            return sph::set_last_error(SPH_E_NOMEM, "slpv_lbfgs: cudaMalloc failed");
+        SCK(cudaMemset(m->lb, 0, n * sizeof(double)));
+    }
+    LbDev L;
+    L.W = m->lb;
+    L.g = L.W + kLT;
+    L.d = L.g + kLT;
+    L.S = L.d + kLT;
+    L.Y = L.S + (size_t)kLM * kLT;
+    L.rho = L.Y + (size_t)kLM * kLT;
+    L.gd = L.rho + kLM;
+    L.count = m->lb_count;
+    L.N = m->N;
+    auto eval = [&](bool grad, double* f) -> int {
+        int r = loss_grad_launch(m, u, y, n_traj, T, lti_only != 0, grad ? m->grad : nullptr, st);
+        if (r) return r;
+        SCK(cudaMemcpyAsync(f, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));
+        return SPH_OK;
+    };
+    double f = 0.0;
+    if ((rc = eval(true, &f))) return rc;
+    if (!std::isfinite(f)) return sph::set_last_error(SPH_E_DIVERGED, "slpv_lbfgs: the loss at the start is not finite");
+    lb_init_kernel<<<1, kLT, 0, st>>>(m->th, m->grad, L);
+    SCK(cudaGetLastError());
+    constexpr double kArmijo = 1e-4;
+    int it = 0;
+    for (; it < iters; ++it) {
+        lb_dir_kernel<<<1, kLT, 0, st>>>(L);
+        SCK(cudaGetLastError());
+        double gd[2];
+        int cnt[2];
+        SCK(cudaMemcpyAsync(gd, L.gd, sizeof(gd), cudaMemcpyDeviceToHost, st));
+        SCK(cudaMemcpyAsync(cnt, L.count, sizeof(cnt), cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));
+        if (!(gd[0] < 0.0)) break;  // stationary
+        double step = cnt[0] > 0 ? 1.0 : std::min(1.0, 0.01 / std::sqrt(gd[1]));  // after a reset: 0.01 in theta
+        bool ok = false;
+        double fn = 0.0;
+        for (int tries = 0; tries < 40; ++tries) {
+            lb_try_kernel<<<1, kLT, 0, st>>>(m->th, L, step);
+            SCK(cudaGetLastError());
+            if ((rc = eval(false, &fn))) return rc;
+            if (std::isfinite(fn) && fn <= f + kArmijo * step * gd[0]) {
+                ok = true;
+                break;
+            }
+            step *= 0.5;
+        }
+        if (!ok) {  // no decrease along d: back to the last accepted point
+            lb_try_kernel<<<1, kLT, 0, st>>>(m->th, L, 0.0);
+            SCK(cudaGetLastError());
+            break;
+        }
+        if ((rc = eval(true, &fn))) return rc;
+        lb_accept_kernel<<<1, kLT, 0, st>>>(m->grad, L, step);
+        SCK(cudaGetLastError());
+        f = fn;
+        if (loss_hist) loss_hist[it] = f;
+    }
+    if (loss_hist)
+        for (int k = it; k < iters; ++k) loss_hist[k] = f;
+    SCK(cudaStreamSynchronize(st));
+    return SPH_OK;
+}
+
+int slpv_init_ls(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, void* stream)
+{
+    int rc = check_data(m, u, n_traj, T);
+    if (rc) return rc;
+    if (!y || T < 2) return inval("slpv_init_ls: NULL y or T < 2");
+    if (m->cfg.nx < 3) return inval("slpv_init_ls: the start needs nx >= 3 (the velocities are states)");
+    cudaStream_t st = (cudaStream_t)stream;
+    constexpr int nblk = 152;
+    double* part = nullptr;
+    int* status = nullptr;
+    SCK(cudaMalloc(&part, (size_t)nblk * kLsVals * sizeof(double)));
+    cudaError_t e = cudaMalloc(&status, sizeof(int));
+    if (e != cudaSuccess) {
+        cudaFree(part);
+        return sph::set_last_error(SPH_E_NOMEM, "slpv_init_ls: cudaMalloc failed");
+    }
+    ls_gram_kernel<<<nblk, kLsThreads, 0, st>>>(u, y, m->scales, n_traj, T, part);
+    e = by_nx(m->cfg.nx, [&](auto c) {
+        constexpr int NX = decltype(c)::value;
+        ls_solve_kernel<NX><<<1, 128, 0, st>>>(part, nblk, m->th, status);
+        return cudaGetLastError();
+    });
+    int hs = 1;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(part);
+    cudaFree(status);
+    SCK(e);
+    if (hs != 0) return sph::set_last_error(SPH_E_DIVERGED, "slpv_init_ls: the normal equations are singular");
     return SPH_OK;
 }
 

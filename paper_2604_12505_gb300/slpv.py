@@ -79,6 +79,12 @@ class VelocityModel:
         check(lib().slpv_normalize(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], _stream(stream)),
               "slpv_normalize")
 
+    def init_ls(self, u, y, stream=None):
+        """Least-squares LTI start of M_0 (first-order ARX on the scaled data)."""
+        u, y = self._data(u), self._data(y)
+        check(lib().slpv_init_ls(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], _stream(stream)),
+              "slpv_init_ls")
+
     def loss_grad(self, u, y, lti_only: bool = False, grad: bool = True, stream=None):
         u, y = self._data(u), self._data(y)
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -93,6 +99,14 @@ class VelocityModel:
         hist = torch.zeros(max(iters, 1), dtype=torch.float64, device="cuda")
         check(lib().slpv_train(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], iters, lr, int(lti_only),
                                _ptr(hist), _stream(stream)), "slpv_train")
+        return hist[:iters]
+
+    def lbfgs(self, u, y, iters: int, lti_only: bool = False, stream=None):
+        """L-BFGS iterations; returns the accepted loss per iteration (host)."""
+        u, y = self._data(u), self._data(y)
+        hist = np.zeros(max(iters, 1), dtype=np.float64)
+        check(lib().slpv_lbfgs(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], iters, int(lti_only),
+                               hist.ctypes.data, _stream(stream)), "slpv_lbfgs")
         return hist[:iters]
 
     # -- use ---------------------------------------------------------------------
@@ -133,8 +147,9 @@ def layout(nx: int) -> dict:
 
 def initial_theta(nx: int, seed: int, base=None, m1_std: float = 1e-2, a0: float = 0.9,
                   bc_std: float = 0.1) -> np.ndarray:
-    """Starting point of a fit (Section 5.3.2).  Without `base` (the LTI
-    stage): A_0 = a0 I, B_0 and C_0 ~ N(0, bc_std^2), everything else zero.
+    """Starting point of a fit (Section 5.3.2).  Without `base` (an LTI
+    start drawn at random; the least-squares start is ``init_ls``): A_0 =
+    a0 I, B_0 and C_0 ~ N(0, bc_std^2), everything else zero.
     With `base` (an LPV restart): M_0 from base; the B and C blocks of M_1
     ~ N(0, m1_std^2) and its A block zero, so that A(p) = A_0 keeps the start's
     spectrum; network weights by Xavier's uniform rule, biases zero."""

@@ -140,3 +140,26 @@ def test_closed_loop_of_a_rigid_body_model_is_the_discrete_pd_loop():
     # thetadot sample of step k is C x_k with x_k the rate before the kick of step k
     np.testing.assert_allclose(out[:, 5], traj[:, 1], rtol=0, atol=1e-12)
     assert abs(out[-1, 2] - 0.3) < 1e-3  # the loop settles on the reference
+
+
+def test_ls_start_recovers_a_first_order_system_exactly():
+    """Noise-free data of y_{k+1} = A1 y_k + B1 u_k (y_0 = 0) give back A1 and
+    B1, and the realised start reproduces the data in free run."""
+    rng = np.random.default_rng(30)
+    A1 = np.diag([0.99, 0.95, 0.9]) + 0.01 * rng.normal(size=(3, 3))
+    B1 = rng.normal(0, 0.2, (3, 3))
+    U, Y = [], []
+    for _ in range(3):
+        u = rng.normal(size=(40, NU))
+        y = np.zeros((40, NY))
+        for k in range(39):
+            y[k + 1] = A1 @ y[k] + B1 @ u[k]
+        U.append(u)
+        Y.append(y)
+    th = S.ls_start(U, Y, NX)
+    P = S.unpack(th, NX, NU, NY)
+    np.testing.assert_allclose(P["M0"][:3, :3], A1, atol=1e-10)
+    np.testing.assert_allclose(P["M0"][:3, NX:], B1, atol=1e-10)
+    assert np.all(P["M0"][3, :] == 0) and np.all(P["M1"] == 0)
+    yh, _, _ = S.simulate(th, U[0], NX, NY)
+    np.testing.assert_allclose(yh, Y[0], atol=1e-9)

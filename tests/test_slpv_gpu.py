@@ -154,3 +154,47 @@ def test_first_adam_step_and_training_descends():
     th, _ = m.get_params()
     assert np.all(th[~mask] == 0)
     m.close()
+
+
+def test_lbfgs_never_raises_the_loss_and_refines_adam():
+    torch = need_gpu()
+    from paper_2604_12505_gb300.slpv import VelocityModel
+    sc = np.array([20.0, 20.0, 2.0, 0.1, 0.1, 0.05], dtype=np.float32)
+    teacher = _theta(4, 21, m1=0.1)[1]
+    u, _ = _data(12, 80, 22, sc)
+    mt = VelocityModel(nx=4)
+    mt.set_params(teacher, sc)
+    y, _ = mt.predict(torch.tensor(u), Ts=0.05)
+    mt.close()
+    m = VelocityModel(nx=4, sigma2=1e-6)
+    m.set_params(_theta(4, 23, m1=0.05)[1], sc)
+    m.train(torch.tensor(u), y, iters=100, lr=3e-3)
+    l0 = float(m.loss_grad(torch.tensor(u), y, grad=False)[0].item())
+    hist = m.lbfgs(torch.tensor(u), y, iters=40)
+    l1 = float(m.loss_grad(torch.tensor(u), y, grad=False)[0].item())
+    assert np.all(np.diff(hist) <= 0) and hist[0] <= l0 and l1 == pytest.approx(hist[-1], rel=1e-12)
+    assert l1 < 0.9 * l0
+    th, _ = m.get_params()
+    assert np.all(th[S.d_mask(4, NU, NY) == 0] == 0)
+    m.close()
+
+
+def test_least_squares_start_matches_oracle():
+    torch = need_gpu()
+    from paper_2604_12505_gb300.slpv import VelocityModel
+    sc = np.array([20.0, 20.0, 2.0, 0.1, 0.1, 0.05], dtype=np.float32)
+    teacher = _theta(4, 31, m1=0.1)[1]
+    u, _ = _data(10, 150, 32, sc)
+    mt = VelocityModel(nx=4)
+    mt.set_params(teacher, sc)
+    y, _ = mt.predict(torch.tensor(u), Ts=0.05)
+    mt.close()
+    yn = y.cpu().numpy()
+    m = VelocityModel(nx=4)
+    m.set_params(None, sc)
+    m.init_ls(torch.tensor(u), y)
+    th, _ = m.get_params()
+    ref = S.ls_start([u[i].astype(np.float64) / sc[:3] for i in range(10)],
+                     [yn[i].astype(np.float64) / sc[3:] for i in range(10)], 4)
+    assert np.abs(th - ref).max() <= 1e-5 * np.abs(ref).max()
+    m.close()
