@@ -72,11 +72,12 @@ int slpv_init_ls(slpv_model* m, const float* u, const float* y, int32_t n_traj, 
  *   J = mean over the n_traj * T samples of ||y_k / s_y - y_hat_k||^2 + sigma2/2 ||theta||^2
  * and its gradient by backpropagation through time, through the state
  * recursion and the scheduling map.  loss_out: device double [1]; grad_out:
- * device float [n_theta] or NULL (loss only).  lti_only != 0 zeroes the
- * gradient of M_1 and of the network (the LTI stage).  Sums are taken in a
- * fixed order: results are deterministic.
+ * device float [n_theta] or NULL (loss only).  stage selects the entries
+ * that train (the others get a zero gradient): 0 all, 1 M_0 only (the LTI
+ * stage), 2 M_1 and the network only (M_0 held).  SPH_E_INVAL for another
+ * value.  Sums are taken in a fixed order: results are deterministic.
  */
-int slpv_loss_grad(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t lti_only,
+int slpv_loss_grad(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t stage,
                    double* loss_out, float* grad_out, void* stream);
 
 /*
@@ -84,22 +85,23 @@ int slpv_loss_grad(slpv_model* m, const float* u, const float* y, int32_t n_traj
  * theta from its current value; loss_hist: device double [iters] or NULL,
  * the loss at each iterate.  A step whose loss is not finite or exceeds ten
  * times the last accepted loss is undone and retried at half the step.
- * lti_only as in slpv_loss_grad.
+ * stage as in slpv_loss_grad.
  */
 int slpv_train(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t iters, float lr,
-               int32_t lti_only, double* loss_hist, void* stream);
+               int32_t stage, double* loss_hist, void* stream);
 
 /*
  * L-BFGS refinement after Adam (Section 5.3.2): up to iters iterations from
  * the current theta; the two-loop recursion over the last 10 curvature pairs
  * runs in FP64 on the device, the step is 1 (0.01 / |g| after a reset)
  * halved until Armijo's condition (1e-4) holds.  Stops early at a point
- * without descent.  loss_hist: HOST double [iters] or NULL (the accepted
- * loss per iteration, the last one repeated after a stop).  Blocks.
+ * without descent; stage as in slpv_loss_grad.  loss_hist: HOST double
+ * [iters] or NULL (the accepted loss per iteration, the last one repeated
+ * after a stop).  Blocks.
  * SPH_E_DIVERGED: the loss at the start is not finite.
  */
 int slpv_lbfgs(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t iters,
-               int32_t lti_only, double* loss_hist, void* stream);
+               int32_t stage, double* loss_hist, void* stream);
 
 /*
  * Free run of the augmented surrogate from rest over u [n_traj, T, 3]

@@ -46,16 +46,21 @@ inline int n_params(int nx)
     return 2 * no * nz + NH * nz + NH + NH * NH + NH + NH + 1;
 }
 
-// Whether theta[q] is trained: not on a D block; in the LTI stage only M_0.
-__host__ __device__ inline bool trainable(int q, int nx, bool lti_only)
+// Training stages: which entries of theta move (never the D blocks).
+enum { kStageAll = 0, kStageLti = 1, kStageScheduling = 2 };
+
+// Whether theta[q] is trained in `stage`: all entries, M_0 only (the LTI
+// stage), or M_1 and the network only (M_0 held).
+__host__ __device__ inline bool trainable(int q, int nx, int stage)
 {
     const int nz = nx + NU, nm = (nx + NY) * nz;
     if (q < 2 * nm) {
-        if (lti_only && q >= nm) return false;
+        if (stage == kStageLti && q >= nm) return false;
+        if (stage == kStageScheduling && q < nm) return false;
         const int r = (q % nm) / nz, j = (q % nm) % nz;
         return !(r >= nx && j >= nx);
     }
-    return !lti_only;
+    return stage != kStageLti;
 }
 
 // Scheduling map eta(z) = w3 . tanh(W2 tanh(W1 z + b1) + b2) + b3.
@@ -244,7 +249,7 @@ __global__ void __launch_bounds__(kThreads) grad_kernel(const float* __restrict_
 // Sums the block partials in block order, adds the l2 term, masks the fixed
 // entries: loss = sum_sq * inv_n + sigma2/2 |theta|^2, grad = sum + sigma2 theta.
 __global__ void final_kernel(const double* __restrict__ part, int nblk, int N, int nx, const float* __restrict__ theta,
-                             float sigma2, double inv_n, int want_grad, int lti_only, double* __restrict__ loss,
+                             float sigma2, double inv_n, int want_grad, int stage, double* __restrict__ loss,
                              float* __restrict__ grad)
 {
     __shared__ double sq[512];
@@ -257,7 +262,7 @@ __global__ void final_kernel(const double* __restrict__ part, int nblk, int N, i
             double g = 0.0;
             for (int b = 0; b < nblk; ++b) g += part[(size_t)b * (N + 1) + q];
             g += (double)sigma2 * th;
-            grad[q] = trainable(q, nx, lti_only != 0) ? (float)g : 0.f;
+            grad[q] = trainable(q, nx, stage) ? (float)g : 0.f;
         }
     }
     sq[q] = t2;
@@ -743,7 +748,7 @@ int reserve(slpv_model* m, int n_traj, int T, bool grad)
 }
 
 // Launches the loss (and gradient) into m->loss / grad_out.
-int loss_grad_launch(slpv_model* m, const float* u, const float* y, int n_traj, int T, bool lti_only, float* grad_out,
+int loss_grad_launch(slpv_model* m, const float* u, const float* y, int n_traj, int T, int stage, float* grad_out,
                      cudaStream_t st)
 {
     const bool want = grad_out != nullptr;
@@ -762,7 +767,7 @@ int loss_grad_launch(slpv_model* m, const float* u, const float* y, int n_traj, 
     });
     SCK(e);
     final_kernel<<<1, 512, 0, st>>>(m->part, nblk, m->N, m->cfg.nx, m->th, m->cfg.sigma2, 1.0 / ((double)n_traj * T),
-                                    want ? 1 : 0, lti_only ? 1 : 0, m->loss, grad_out);
+                                    want ? 1 : 0, stage, m->loss, grad_out);
     SCK(cudaGetLastError());
     return SPH_OK;
 }
@@ -842,7 +847,7 @@ int slpv_set_params(slpv_model* m, const float* theta, const float* scales)
     if (theta) {
         std::vector<float> h(theta, theta + m->N);
         for (int q = 0; q < m->N; ++q)
-            if (q < 2 * (m->cfg.nx + NY) * (m->cfg.nx + NU) && !trainable(q, m->cfg.nx, false)) h[q] = 0.f;
+            if (q < 2 * (m->cfg.nx + NY) * (m->cfg.nx + NU) && !trainable(q, m->cfg.nx, kStageAll)) h[q] = 0.f;
         SCK(cudaMemcpy(m->th, h.data(), m->N * sizeof(float), cudaMemcpyHostToDevice));
     }
     if (scales) {
@@ -879,25 +884,27 @@ int slpv_normalize(slpv_model* m, const float* u, const float* y, int32_t n_traj
     return SPH_OK;
 }
 
-int slpv_loss_grad(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t lti_only,
+int slpv_loss_grad(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t stage,
                    double* loss_out, float* grad_out, void* stream)
 {
     int rc = check_data(m, u, n_traj, T);
     if (rc) return rc;
     if (!y || !loss_out) return inval("slpv_loss_grad: NULL y or loss_out");
+    if (stage < 0 || stage > 2) return inval("slpv_loss_grad: stage must be 0, 1 or 2");
     cudaStream_t st = (cudaStream_t)stream;
-    rc = loss_grad_launch(m, u, y, n_traj, T, lti_only != 0, grad_out, st);
+    rc = loss_grad_launch(m, u, y, n_traj, T, stage, grad_out, st);
     if (rc) return rc;
     SCK(cudaMemcpyAsync(loss_out, m->loss, sizeof(double), cudaMemcpyDeviceToDevice, st));
     return SPH_OK;
 }
 
 int slpv_train(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t iters, float lr,
-               int32_t lti_only, double* loss_hist, void* stream)
+               int32_t stage, double* loss_hist, void* stream)
 {
     int rc = check_data(m, u, n_traj, T);
     if (rc) return rc;
     if (!y || iters < 0 || !(lr > 0.0f)) return inval("slpv_train: NULL y, iters < 0 or lr <= 0");
+    if (stage < 0 || stage > 2) return inval("slpv_train: stage must be 0, 1 or 2");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nb = (size_t)m->N * sizeof(float);
     const float one = 1.0f;
@@ -911,7 +918,7 @@ int slpv_train(slpv_model* m, const float* u, const float* y, int32_t n_traj, in
     const int threads = ((m->N + 31) / 32) * 32;
     AdamDev A{m->th, m->m, m->v, m->thb, m->lr_scale, m->acc_loss, m->t};
     for (int it = 0; it < iters; ++it) {
-        rc = loss_grad_launch(m, u, y, n_traj, T, lti_only != 0, m->grad, st);
+        rc = loss_grad_launch(m, u, y, n_traj, T, stage, m->grad, st);
         if (rc) return rc;
         adam_kernel<<<1, threads, 0, st>>>(A, m->grad, m->loss, loss_hist, it, m->N, lr);
         SCK(cudaGetLastError());
@@ -922,11 +929,12 @@ int slpv_train(slpv_model* m, const float* u, const float* y, int32_t n_traj, in
 }
 
 int slpv_lbfgs(slpv_model* m, const float* u, const float* y, int32_t n_traj, int32_t T, int32_t iters,
-               int32_t lti_only, double* loss_hist, void* stream)
+               int32_t stage, double* loss_hist, void* stream)
 {
     int rc = check_data(m, u, n_traj, T);
     if (rc) return rc;
     if (!y || iters < 0) return inval("slpv_lbfgs: NULL y or iters < 0");
+    if (stage < 0 || stage > 2) return inval("slpv_lbfgs: stage must be 0, 1 or 2");
     cudaStream_t st = (cudaStream_t)stream;
     if (!m->lb) {
         const size_t n = (size_t)kLT * (3 + 2 * kLM) + kLM + 2;
@@ -945,7 +953,7 @@ int slpv_lbfgs(slpv_model* m, const float* u, const float* y, int32_t n_traj, in
     L.count = m->lb_count;
     L.N = m->N;
     auto eval = [&](bool grad, double* f) -> int {
-        int r = loss_grad_launch(m, u, y, n_traj, T, lti_only != 0, grad ? m->grad : nullptr, st);
+        int r = loss_grad_launch(m, u, y, n_traj, T, stage, grad ? m->grad : nullptr, st);
         if (r) return r;
         SCK(cudaMemcpyAsync(f, m->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
         SCK(cudaStreamSynchronize(st));

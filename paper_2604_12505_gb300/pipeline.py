@@ -432,8 +432,9 @@ def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int 
 
 
 def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int = 2200, relax: int = 20_000,
-                             lti_iters: int = 1000, lti_lr: float = 1e-3, adam_iters: int = 2000, lr: float = 1e-3,
-                             lbfgs_iters: int = 100, restarts: int = 8, cl_samples: int = 600, n_sims: int = 65_536,
+                             lti_iters: int = 1000, lti_lr: float = 1e-3, adam_iters: int = 0, lr: float = 1e-4,
+                             lbfgs_iters: int = 1000, m1_std: float = 1e-3, restarts: int = 8, cl_samples: int = 600,
+                             n_sims: int = 65_536,
                              nx: int = 4,
                              sigma2: float = 1e-4, seed: int = 0, log=None) -> dict:
     """The paper's identification study (Section 5.3) on its spacecraft.
@@ -448,8 +449,9 @@ def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int 
        network, D = 0): an LTI stage (M_0 only: the least-squares ARX start,
        then Adam on the free-run loss) stands in for the ssest fit; then
        `restarts` LPV fits from it with random
-       M_1 and Xavier network weights, Adam then L-BFGS, the lowest training
-       loss kept.
+       M_1 (B and C blocks ~ N(0, m1_std^2)) and Xavier network weights:
+       adam_iters Adam steps on M_1 and the network (M_0 held; none by
+       default), then L-BFGS on all of theta; the lowest training loss kept.
     3. Validation as in Table 3: n_val closed-loop manoeuvres of
        cl_samples * T_s seconds (the PD law of Eq. 28 tracking random attitude
        steps, piecewise forces and torques) flown by the SPH simulator and by
@@ -480,22 +482,26 @@ def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int 
     t1 = time.perf_counter()
     m.init_ls(u, y)
     fits = dict(ls=dict(loss=float(m.loss_grad(u, y, grad=False)[0].item())))
-    h = m.train(u, y, lti_iters, lti_lr, lti_only=True).cpu().numpy() if lti_iters > 0 else np.array([np.nan])
+    h = m.train(u, y, lti_iters, lti_lr, stage=m.LTI).cpu().numpy() if lti_iters > 0 else np.array([np.nan])
     th_lti, _ = m.get_params()
     fits["lti"] = dict(loss=float(m.loss_grad(u, y, grad=False)[0].item()), seconds=time.perf_counter() - t1)
     best = None
     for r in range(restarts):
         t2 = time.perf_counter()
-        m.set_params(initial_theta(nx, seed=seed * 100 + r + 1, base=th_lti), sc)
-        h = m.train(u, y, adam_iters, lr).cpu().numpy()
+        m.set_params(initial_theta(nx, seed=seed * 100 + r + 1, base=th_lti, m1_std=m1_std), sc)
+        l0 = float(m.loss_grad(u, y, grad=False)[0].item())
+        # Adam on the scheduling part (M_0 held at the LTI fit), then L-BFGS on everything
+        if adam_iters > 0:
+            m.train(u, y, adam_iters, lr, stage=m.SCHEDULING)
         if lbfgs_iters > 0 and np.isfinite(float(m.loss_grad(u, y, grad=False)[0].item())):
             m.lbfgs(u, y, lbfgs_iters)
         loss = float(m.loss_grad(u, y, grad=False)[0].item())
-        say("velocity surrogate: restart", r, loss, time.perf_counter() - t2)
+        fits.setdefault("restart_losses", []).append([l0, loss])
+        say("velocity surrogate: restart", r, l0, loss, time.perf_counter() - t2)
         if np.isfinite(loss) and (best is None or loss < best[0]):
             best = (loss, m.get_params()[0])
     fits["lpv"] = dict(loss=best[0] if best else float("nan"), seconds=time.perf_counter() - t1 - fits["lti"]["seconds"],
-                       restarts=restarts, adam_iters=adam_iters, lbfgs_iters=lbfgs_iters)
+                       restarts=restarts, adam_iters=adam_iters, lbfgs_iters=lbfgs_iters, m1_std=m1_std)
     out["fit"] = fits
     # training-set BFR of the free run (velocities)
     yv = ys[:, :, 3:6]

@@ -85,27 +85,31 @@ class VelocityModel:
         check(lib().slpv_init_ls(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], _stream(stream)),
               "slpv_init_ls")
 
-    def loss_grad(self, u, y, lti_only: bool = False, grad: bool = True, stream=None):
+    # training stages: which entries of theta move
+    ALL, LTI, SCHEDULING = 0, 1, 2
+
+    def loss_grad(self, u, y, stage: int = 0, grad: bool = True, stream=None):
         u, y = self._data(u), self._data(y)
         loss = torch.zeros(1, dtype=torch.float64, device="cuda")
         g = torch.zeros(self.n, dtype=torch.float32, device="cuda") if grad else None
-        check(lib().slpv_loss_grad(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], int(lti_only), _ptr(loss),
+        check(lib().slpv_loss_grad(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], stage, _ptr(loss),
                                    _ptr(g), _stream(stream)), "slpv_loss_grad")
         return loss, g
 
-    def train(self, u, y, iters: int, lr: float, lti_only: bool = False, stream=None):
-        """Adam steps; returns the loss at every iterate (device float64 [iters])."""
+    def train(self, u, y, iters: int, lr: float, stage: int = 0, stream=None):
+        """Adam steps on the entries of `stage`; returns the loss at every
+        iterate (device float64 [iters])."""
         u, y = self._data(u), self._data(y)
         hist = torch.zeros(max(iters, 1), dtype=torch.float64, device="cuda")
-        check(lib().slpv_train(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], iters, lr, int(lti_only),
+        check(lib().slpv_train(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], iters, lr, stage,
                                _ptr(hist), _stream(stream)), "slpv_train")
         return hist[:iters]
 
-    def lbfgs(self, u, y, iters: int, lti_only: bool = False, stream=None):
+    def lbfgs(self, u, y, iters: int, stage: int = 0, stream=None):
         """L-BFGS iterations; returns the accepted loss per iteration (host)."""
         u, y = self._data(u), self._data(y)
         hist = np.zeros(max(iters, 1), dtype=np.float64)
-        check(lib().slpv_lbfgs(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], iters, int(lti_only),
+        check(lib().slpv_lbfgs(self._h, _ptr(u), _ptr(y), u.shape[0], u.shape[1], iters, stage,
                                hist.ctypes.data, _stream(stream)), "slpv_lbfgs")
         return hist[:iters]
 

@@ -62,11 +62,14 @@ def test_loss_and_gradient_match_oracle(nx):
     assert float(l2.item()) == loss and np.array_equal(g2.cpu().numpy(), g)  # fixed-order sums
     mask = S.d_mask(nx, NU, NY)
     assert np.all(g[mask == 0] == 0)
-    # the LTI stage trains M_0 only
-    _, gl = m.loss_grad(torch.tensor(u), torch.tensor(y), lti_only=True)
-    gl = gl.cpu().numpy()
+    # the LTI stage trains M_0 only, the scheduling stage everything else
     nm = (nx + NY) * (nx + NU)
+    _, gl = m.loss_grad(torch.tensor(u), torch.tensor(y), stage=m.LTI)
+    gl = gl.cpu().numpy()
     assert np.all(gl[nm:] == 0) and np.array_equal(gl[:nm], g[:nm])
+    _, gs = m.loss_grad(torch.tensor(u), torch.tensor(y), stage=m.SCHEDULING)
+    gs = gs.cpu().numpy()
+    assert np.all(gs[:nm] == 0) and np.array_equal(gs[nm:], g[nm:])
     m.close()
 
 
