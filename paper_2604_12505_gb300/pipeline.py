@@ -433,7 +433,7 @@ def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int 
 
 def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int = 2200, relax: int = 20_000,
                              lti_iters: int = 1000, lti_lr: float = 1e-3, adam_iters: int = 0, lr: float = 1e-4,
-                             lbfgs_iters: int = 1000, m1_std: float = 1e-3, restarts: int = 8, cl_samples: int = 600,
+                             lbfgs_iters: int = 1000, m1_std: float = 0.0, restarts: int = 8, cl_samples: int = 600,
                              n_sims: int = 65_536,
                              nx: int = 4,
                              sigma2: float = 1e-4, seed: int = 0, log=None) -> dict:
@@ -448,8 +448,9 @@ def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int 
     2. The self-scheduled LPV model (n_x = 4, n_p = 1, eta a 2 x 4 tanh
        network, D = 0): an LTI stage (M_0 only: the least-squares ARX start,
        then Adam on the free-run loss) stands in for the ssest fit; then
-       `restarts` LPV fits from it with random
-       M_1 (B and C blocks ~ N(0, m1_std^2)) and Xavier network weights:
+       `restarts` LPV fits from it with M_1's B and C blocks ~ N(0, m1_std^2)
+       (zero by default: the restart starts on the LTI fit, where the
+       gradient of M_1 is already nonzero) and Xavier network weights:
        adam_iters Adam steps on M_1 and the network (M_0 held; none by
        default), then L-BFGS on all of theta; the lowest training loss kept.
     3. Validation as in Table 3: n_val closed-loop manoeuvres of

@@ -201,3 +201,36 @@ def test_least_squares_start_matches_oracle():
                      [yn[i].astype(np.float64) / sc[3:] for i in range(10)], 4)
     assert np.abs(th - ref).max() <= 1e-5 * np.abs(ref).max()
     m.close()
+
+
+def test_scheduling_network_gains_over_the_lti_fit_when_the_system_is_scheduled():
+    """On data of a strongly scheduled teacher, the LPV fit started on the best
+    LTI fit (M_1 = 0, random network, then L-BFGS on all of theta) ends well
+    below the LTI loss: what the trained network adds over the model without it."""
+    torch = need_gpu()
+    from paper_2604_12505_gb300.slpv import VelocityModel, initial_theta
+    sc = np.array([20.0, 20.0, 2.0, 0.1, 0.1, 0.05], dtype=np.float32)
+    teacher = _theta(4, 41, m1=0.3)[1]
+    u, _ = _data(16, 120, 42, sc)
+    mt = VelocityModel(nx=4)
+    mt.set_params(teacher, sc)
+    y, _ = mt.predict(torch.tensor(u), Ts=0.05)
+    mt.close()
+    ut = torch.tensor(u)
+    m = VelocityModel(nx=4, sigma2=1e-6)
+    m.normalize(ut, y)
+    _, s = m.get_params()
+    m.init_ls(ut, y)
+    m.train(ut, y, iters=300, lr=1e-3, stage=m.LTI)
+    m.lbfgs(ut, y, iters=100, stage=m.LTI)
+    l_lti = float(m.loss_grad(ut, y, grad=False)[0].item())
+    th_lti, _ = m.get_params()
+    best = np.inf
+    for r in range(3):
+        m.set_params(initial_theta(4, seed=50 + r, base=th_lti, m1_std=0.0), s)
+        l0 = float(m.loss_grad(ut, y, grad=False)[0].item())
+        assert l0 == pytest.approx(l_lti, rel=1e-3)  # the restart starts on the LTI fit (plus the l2 term of the network)
+        m.lbfgs(ut, y, iters=300)
+        best = min(best, float(m.loss_grad(ut, y, grad=False)[0].item()))
+    assert best < 0.8 * l_lti, (best, l_lti)
+    m.close()
