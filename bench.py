@@ -11,7 +11,9 @@ fluid-ghost pairs with r < h, counted exactly by the force kernel).  After
 the timed region, the ``surrogate`` object reports the second half of the
 metric: closed-loop simulations per second of the LPV surrogate against the
 SPH simulator on 64 held-out manoeuvres, with the surrogate's NRMSE per body
-channel (data set of 256 batched tanks x 4 launches, dt = 2e-4 s).
+channel (data set of 256 batched tanks x 4 launches, dt = 2e-4 s); the
+``velocity_surrogate`` object does the same for the paper's own model
+(velocity level, scheduled by a tanh network) on the paper's spacecraft.
 
 Arms:
   default            the CUDA library; prints one JSON line (rank 0).
@@ -250,6 +252,36 @@ def surrogate(size: str) -> dict:
     }
 
 
+VELOCITY_SIZES = {
+    # 24 identification trains of 2200 samples (110 s) on the Tables 1-2
+    # spacecraft; 8 held-out closed-loop manoeuvres of 30 s; 65,536 surrogate runs
+    "full": dict(n_train=24, n_val=8, id_samples=2200, relax=20_000, n_sims=65_536),
+    "small": dict(n_train=8, n_val=4, id_samples=1100, relax=10_000, restarts=2, n_sims=65_536),
+}
+
+
+def velocity_surrogate(size: str) -> dict:
+    """The paper's own surrogate (velocity level, self-scheduled) on the
+    paper's spacecraft: closed-loop flights per second against the simulator
+    on held-out manoeuvres, with NRMSE = 1 - BFR / 100 per channel."""
+    from paper_2604_12505_gb300 import pipeline
+
+    t0 = time.perf_counter()
+    r = pipeline.velocity_surrogate_study(**VELOCITY_SIZES[size])
+    th, val = r["throughput"], r["validation"]
+    nrmse = {m: {c: 1.0 - v / 100.0 for c, v in val[m].items()} for m in ("lpv", "lti")}
+    return {
+        "size": size,
+        "surrogate_sims_per_s": th["surrogate_sims_per_s"], "sph_sims_per_s": th["sph_flights_per_s"],
+        "speedup": th["speedup"], "nrmse": nrmse["lpv"], "nrmse_lti": nrmse["lti"],
+        "max_nrmse": max(nrmse["lpv"].values()), "max_nrmse_lti": max(nrmse["lti"].values()),
+        "closed_loop": {"sims": th["surrogate_sims"], "samples": th["samples"], "Ts": r["Ts"],
+                        "seconds": val["seconds"], "surrogate_s": th["surrogate_s"], "sph_s": val["sph_device_s"]},
+        "fit": {k: {"loss": v["loss"]} for k, v in r["fit"].items() if isinstance(v, dict) and "loss" in v},
+        "wall_s": time.perf_counter() - t0,
+    }
+
+
 def combine_ranks(seconds: float, units: float, device) -> tuple[float, float]:
     """Whole-job time and work of independent replicas: the maximum time and
     the summed units over the ranks of the default process group (the
@@ -398,6 +430,7 @@ def run_ours(a):
     sim.close()
     if a.surrogate != "off":
         out["surrogate"] = surrogate(a.surrogate)
+        out["velocity_surrogate"] = velocity_surrogate(a.surrogate)
     if not a.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(cfg, a.cpu_seconds)
     print(json.dumps(out), flush=True)
