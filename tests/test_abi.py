@@ -40,3 +40,21 @@ def test_binding_raises_without_gpu_or_library(monkeypatch):
     monkeypatch.setattr(_lib, "LIB_PATH", "/nonexistent/libgb300sloshing.so")
     with pytest.raises(ImportError):
         _lib.lib()
+
+
+def test_argument_checks_answer_without_a_gpu():
+    """Entry points reject bad arguments before touching the device."""
+    import ctypes as C
+    from paper_2604_12505_gb300 import build
+    from paper_2604_12505_gb300._lib import SphParams
+    lib = C.CDLL(build.build())
+    n = C.c_int32()
+    for nx, want in ((2, 2 * 25 + 20 + 29), (4, 155), (6, 2 * 81 + 36 + 29), (8, 315)):
+        assert lib.slpv_n_params(nx, C.byref(n)) == 0 and n.value == want
+    assert lib.slpv_n_params(3, C.byref(n)) == -1
+    out = C.c_void_p()
+    assert lib.slpv_create(None, C.byref(out)) == -1
+    p = SphParams(dx=0.01, h_over_dx=1.3, n_rings=0)
+    g = C.c_double()
+    assert lib.sph_gamma1_estimate(C.byref(p), C.byref(g)) == -1
+    assert lib.sph_gamma1_estimate(None, C.byref(g)) == -1
