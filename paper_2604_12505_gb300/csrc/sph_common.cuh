@@ -148,6 +148,7 @@ struct __align__(16) TilePartial {
 };
 
 constexpr int kTileGroup = 64;    // tiles per first-level reduction group
+constexpr int kOneLevelLoads = 8; // one-level reduction up to this many partials per thread of a tile
 constexpr int kNbrMax = 40;       // fluid neighbours recorded per particle by the density pass
 
 // Optional per-particle outputs of an evaluation pass (indexed by particle).

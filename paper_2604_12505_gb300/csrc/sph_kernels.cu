@@ -249,6 +249,28 @@ __device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* one pe
     return r;
 }
 
+// Sum of partials [p0, p1) by the whole block in fixed order: thread t adds
+// p0 + t, p0 + t + blockDim.x, ... in that order, then the block tree (result
+// in thread 0).
+__device__ Red block_reduce_partials(const TilePartial* P, int p0, int p1, bool com, Red* scratch)
+{
+    const F2 z{0.f, 0.f};
+    Red r{z, z, z, z, z, 0ull};
+    for (int i = p0 + (int)threadIdx.x; i < p1; i += blockDim.x) {
+        const float4 a = __ldcg(&P[i].a), b = __ldcg(&P[i].b);
+        const int4 c = __ldcg(&P[i].c);
+        r.fx = f2_add(r.fx, F2{a.x, a.y});
+        r.fy = f2_add(r.fy, F2{a.z, a.w});
+        r.t = f2_add(r.t, F2{b.x, b.y});
+        if (com) {
+            r.cx = f2_add(r.cx, F2{b.z, b.w});
+            r.cy = f2_add(r.cy, F2{__int_as_float(c.x), __int_as_float(c.y)});
+        }
+        r.pairs += (unsigned long long)(unsigned)c.z;
+    }
+    return block_reduce(r, true, com, scratch);
+}
+
 __device__ __forceinline__ void store_partial(TilePartial* P, const Red& r, int wall)
 {
     P->a = make_float4(r.fx.hi, r.fx.lo, r.fy.hi, r.fy.lo);
@@ -284,33 +306,38 @@ __device__ Red warp_reduce_partials(const TilePartial* P, int p0, int p1, bool c
 // ---------------------------------------------------------------------------
 // Body update by the last CTA of a tank (Eq. 20, Eq. 28, outputs)
 // ---------------------------------------------------------------------------
-// Runs in warp 0 of the CTA that completed the tank's last reduction group.
-// The FP64 pipe of this GPU is narrow and every global access on the serial
-// path costs an L2 round trip, so the lanes load the body and input values
-// before the group partials are reduced (the loads overlap the reduction),
-// the body is updated in registers and stored once, and the masses enter as
-// reciprocals.
-__device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
-                              bool sample, bool tan)
+// Runs in warp 0 of the CTA that finished the tank's reduction, with the
+// reduced partials r (and tr, tangent) valid in lane 0.  The FP64 pipe of this
+// GPU is narrow and every global access on the serial path costs an L2 round
+// trip, so the lanes load the body and input values (finalize_preload) before
+// the partials are reduced, the body is updated in registers and stored once,
+// and the masses enter as reciprocals.
+//
+// finalize_preload: lane l of warp 0 loads one value: the body's r, theta,
+// rdot, thetadot, cos, sin (l < 8, the leading doubles of BodyDev), the held
+// control torque (8), the input (9..11); lane 0 collects them.
+__device__ __forceinline__ double finalize_preload(const SimDev& S, int tank)
 {
-    fence_acq_rel();
-    RunDev* run = S.run;
-    BodyDev* bp = S.body + tank;
-    const long long step = run->step, step0 = run->step0;
-    const long long k = step - step0;
-    // lane l loads one value: the body's r, theta, rdot, thetadot, cos, sin
-    // (l < 8, the leading doubles of BodyDev), the held control torque (8),
-    // the input (9..11); lane 0 collects them after the reduction
     const int lane = (int)(threadIdx.x & 31);
+    const RunDev* run = S.run;
+    const BodyDev* bp = S.body + tank;
+    const long long k = run->step - run->step0;
     const double* up = run->u;
     double pre = 0.0;
     if (lane < 8) pre = reinterpret_cast<const double*>(bp)[lane];
     else if (lane == 8) pre = bp->tau_c;
     else if (lane < 12 && up) pre = up[tank * run->u_tank_stride + 3 * k + (lane - 9)];
-    int wall;
-    Red r = warp_reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall);
-    Red tr = r;
-    if (tan) tr = warp_reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall);
+    return pre;
+}
+
+__device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
+                              bool sample, bool tan, const Red& r, const Red& tr, double pre)
+{
+    RunDev* run = S.run;
+    BodyDev* bp = S.body + tank;
+    const long long step = run->step, step0 = run->step0;
+    const long long k = step - step0;
+    const int lane = (int)(threadIdx.x & 31);
     double rx = __shfl_sync(0xffffffffu, pre, 0), ry = __shfl_sync(0xffffffffu, pre, 1);
     double th = __shfl_sync(0xffffffffu, pre, 2), vx = __shfl_sync(0xffffffffu, pre, 3);
     double vy = __shfl_sync(0xffffffffu, pre, 4), w = __shfl_sync(0xffffffffu, pre, 5);
@@ -702,9 +729,31 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     Red r = block_reduce(acc, any_wall, sample, scratch);
     Red tr = r;
     if constexpr (TAN) tr = block_reduce(tacc, any_wall, sample, scratch);
-    // two-level fixed-order reduction: the last tile of a group of
-    // kTileGroup tiles sums the group, the last group of a tank finalizes it
+    // fixed-order reduction of the tile partials.  One level when the tank's
+    // last tile can fetch them with at most kOneLevelLoads loads per thread
+    // (every small tank, the large tank at 8x4): the last tile (by a counter
+    // of finished tiles) sums them with the whole block.  Otherwise two
+    // levels: the last tile of each group of kTileGroup tiles sums the group,
+    // the last group of the tank sums the groups.
     const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
+    if (t1 - t0 <= kOneLevelLoads * (int)blockDim.x) {
+        if (threadIdx.x == 0) {
+            store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
+            if constexpr (TAN) store_partial(S.tpartials + blockIdx.x, tr, any_wall ? 1 : 0);
+            fence_acq_rel();
+            is_last = (atomicAdd(&S.body[tank].done, 1u) == (unsigned)(t1 - t0 - 1));
+        }
+        __syncthreads();
+        if (!is_last) return;
+        fence_acq_rel();
+        double pre = 0.0;
+        if (threadIdx.x < 32) pre = finalize_preload(S, tank);
+        const Red rt = block_reduce_partials(S.partials, t0, t1, sample, scratch);
+        Red trt = rt;
+        if constexpr (TAN) trt = block_reduce_partials(S.tpartials, t0, t1, sample, scratch);
+        if (threadIdx.x < 32) tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN, rt, trt, pre);
+        return;
+    }
     const int gi = (blockIdx.x - t0) / kTileGroup;
     const int gt0 = t0 + gi * kTileGroup, gt1 = min(gt0 + kTileGroup, t1);
     const int g = S.group_first[tank] + gi;
@@ -729,7 +778,14 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         prev = atomicAdd(&S.body[tank].done, 1u);
     }
     const unsigned n_groups = (unsigned)(S.group_first[tank + 1] - S.group_first[tank]);
-    if (__shfl_sync(0xffffffffu, prev, 0) == n_groups - 1) tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN);
+    if (__shfl_sync(0xffffffffu, prev, 0) != n_groups - 1) return;
+    fence_acq_rel();
+    const double pre = finalize_preload(S, tank);
+    int wall_t;
+    const Red rt = warp_reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall_t);
+    Red trt = rt;
+    if constexpr (TAN) trt = warp_reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall_t);
+    tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN, rt, trt, pre);
 }
 
 // ---------------------------------------------------------------------------
