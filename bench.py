@@ -156,7 +156,7 @@ FP32_LANES = 152 * 128
 # tile code, mean of three launches captured warm (ncu --cache-control none):
 # the working set stays in L2.  Valid for the kernel source they were
 # captured on; a tile without a capture reports null.
-FORCE_TRAFFIC_BYTES = {3: 6_485, 4: 7_851}
+FORCE_TRAFFIC_BYTES = {4: 47_104}
 
 
 # --------------------------------------------------------------------------
