@@ -234,3 +234,25 @@ def test_scheduling_network_gains_over_the_lti_fit_when_the_system_is_scheduled(
         best = min(best, float(m.loss_grad(ut, y, grad=False)[0].item()))
     assert best < 0.8 * l_lti, (best, l_lti)
     m.close()
+
+
+@pytest.mark.parametrize("nx,n_traj,T", [(8, 70, 25), (6, 65, 1), (4, 1, 3)])
+def test_gradient_parity_at_edge_sizes(nx, n_traj, T):
+    """The largest state (n_x = 8: 80 KB of per-thread accumulators, above the
+    default shared-memory limit), more trajectories than one block holds (a
+    ragged second block), a single sample, a single trajectory."""
+    torch = need_gpu()
+    from paper_2604_12505_gb300.slpv import VelocityModel
+    sc = np.array([20.0, 20.0, 2.0, 0.1, 0.1, 0.05], dtype=np.float32)
+    th64, th32 = _theta(nx, 60 + nx, m1=0.1)
+    u, y = _data(n_traj, T, 61, sc)
+    U = [u[i].astype(np.float64) / sc[:3] for i in range(n_traj)]
+    Y = [y[i].astype(np.float64) / sc[3:] for i in range(n_traj)]
+    ref_l = S.loss(th64, U, Y, nx, 1e-4)
+    ref_g = S.loss_grad(th64, U, Y, nx, 1e-4, S.d_mask(nx, NU, NY))
+    m = VelocityModel(nx=nx, sigma2=1e-4)
+    m.set_params(th32, sc)
+    loss, g = m.loss_grad(torch.tensor(u), torch.tensor(y))
+    assert abs(float(loss.item()) - ref_l) <= 1e-4 * ref_l
+    assert np.abs(g.cpu().numpy() - ref_g).max() <= 1e-3 * np.abs(ref_g).max()
+    m.close()
