@@ -163,3 +163,28 @@ def test_ls_start_recovers_a_first_order_system_exactly():
     assert np.all(P["M0"][3, :] == 0) and np.all(P["M1"] == 0)
     yh, _, _ = S.simulate(th, U[0], NX, NY)
     np.testing.assert_allclose(yh, Y[0], atol=1e-9)
+
+
+def test_closed_loop_equals_the_free_run_under_the_inputs_it_applied():
+    """With a network that ignores the input, the scheduling at the sample and
+    at the step coincide, so the closed loop (scheduled, M_1 != 0) must equal
+    the open-loop free run and augmentation driven by the inputs the PD law
+    applied, rebuilt from the recorded angle and rate."""
+    th = _random_theta(70, scale_m1=0.3)
+    P = S.unpack(th, NX, NU, NY)
+    P["W1"][:, NX:] = 0.0                       # eta depends on the state only
+    th = S.pack(P)
+    rng = np.random.default_rng(71)
+    T, Ts = 60, 0.05
+    su, sy = np.array([20.0, 20.0, 2.0]), np.array([0.1, 0.1, 0.05])
+    F = rng.uniform(-20, 20, (T, 2))
+    tau = rng.uniform(-2, 2, T)
+    ref = np.full(T, 0.2)
+    pd = dict(J=133.84, omega=0.2 * np.pi, xi=0.7)
+    out = S.closed_loop(th, NX, dict(u=su, y=sy), F, tau, ref, Ts, pd)
+    J, w, xi = pd["J"], pd["omega"], pd["xi"]
+    tc = J * w * w * (ref - out[:, 2]) - 2.0 * xi * J * w * out[:, 5]
+    u = np.column_stack([F, tau + tc]) / su
+    e, yh = S.augment(th, u, NX, NY, Ts)
+    np.testing.assert_allclose(out[:, 3:], yh * sy, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(out[:, :3], e * sy, rtol=0, atol=1e-12)
