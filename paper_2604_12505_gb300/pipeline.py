@@ -534,9 +534,10 @@ def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int 
         out["validation"][name] = bfr
         say("velocity surrogate: closed-loop BFR", name, bfr)
     # throughput of the surrogate closed loop
-    Fb = torch.tensor(np.tile(F, (n_sims // n_val + 1, 1, 1))[:n_sims], device="cuda")
-    tb = torch.tensor(np.tile(tau, (n_sims // n_val + 1, 1))[:n_sims], device="cuda")
-    rb = torch.tensor(np.tile(ref, (n_sims // n_val + 1, 1))[:n_sims], device="cuda")
+    reps = (n_sims + n_val - 1) // n_val  # the validation inputs repeated on the device
+    Fb = torch.tensor(F, device="cuda").repeat(reps, 1, 1)[:n_sims].contiguous()
+    tb = torch.tensor(tau, device="cuda").repeat(reps, 1)[:n_sims].contiguous()
+    rb = torch.tensor(ref, device="cuda").repeat(reps, 1)[:n_sims].contiguous()
     m.simulate(Fb[:64], tb[:64], rb[:64], Ts, cfg["J_body"], ctrl["omega"], ctrl["xi"])
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
