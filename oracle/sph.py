@@ -52,6 +52,7 @@ class Params(C.Structure):
         ("n_rings", C.c_int32),
         ("outer_every", C.c_int32),
         ("ghost_spacing", C.c_double),
+        ("ghost_pressure_clamp", C.c_int32),
     ]
 
 
@@ -91,13 +92,16 @@ def lib():
             L.orc_tank_build.argtypes = [P, dp, dp]
             L.orc_ghost_world.argtypes = [C.c_int, dp, dp, dp, dp, dp]
             L.orc_ghost_world.restype = None
-            L.orc_eval.argtypes = [P, C.c_int, dp, dp, C.c_int, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp, dp]
+            L.orc_eval.argtypes = [P, C.c_int, dp, dp, C.c_int, dp, dp, dp, C.c_int, dp, dp, dp, dp, dp, dp, dp]
             L.orc_shepard.argtypes = [P, C.c_int, dp, dp, dp]
             L.orc_run.argtypes = [P, C.c_int, dp, dp, C.c_int, dp, dp, dp, dp, C.c_int, C.c_int, C.c_double,
                                   C.c_int, dp, dp]
             L.orc_grid_dims.argtypes = [P, dp, dp, ip]
             L.orc_cell_keys_f32.argtypes = [P, C.c_int, fp, C.c_int, C.c_double, C.c_double, ip]
             L.orc_neighbor_counts_f32.argtypes = [P, C.c_int, fp, C.c_int, C.c_int, dp, dp, C.c_int, ip, ip, ip, ip]
+            L.orc_neighbor_counts_f64.argtypes = [P, C.c_int, fp, C.c_int, C.c_int, dp, dp, C.c_int, ip, C.c_double,
+                                                  ip]
+            L.orc_switch_counts.argtypes = [P, C.c_int, dp, dp, C.c_int, dp, dp, ip]
             L.orc_pair_count.argtypes = [P, C.c_int, dp, C.c_int, dp, dp]
             L.orc_pair_count.restype = C.c_longlong
             L.orc_num_threads.argtypes = []
@@ -254,11 +258,15 @@ def evaluate(p: Params, x, v, gB, body, u=(0.0, 0.0, 0.0), brute=False):
     drho = np.zeros(nf)
     fb = np.zeros(3)
     ba = np.zeros(3)
+    fa = np.zeros(6)
     rc = lib().orc_eval(C.byref(p), nf, _d(x), _d(v), ng, _d(gB), _d(body), _d(u), int(brute), _d(rho), _d(P),
-                        _d(acc), _d(drho), _d(fb), _d(ba))
+                        _d(acc), _d(drho), _d(fb), _d(ba), _d(fa))
     if rc:
         raise MemoryError("oracle evaluation failed")
-    return {"rho": rho, "P": P, "acc": acc, "drho": drho, "fb": fb, "body_acc": ba}
+    # fb_abs: [sum |f_x|, sum |f_y|, sum |arm x f|] over the fluid-ghost pair
+    # forces; fb_drho: the same for rho_i df/drho_i (see orc_eval)
+    return {"rho": rho, "P": P, "acc": acc, "drho": drho, "fb": fb, "body_acc": ba, "fb_abs": fa[:3],
+            "fb_drho": fa[3:]}
 
 
 def shepard(p: Params, x, rho):
@@ -299,6 +307,10 @@ def grid_dims(p: Params):
 
 
 def cell_keys_f32(p: Params, xy_f32, anchor):
+    """Cell keys in the kernels' FP32 convention (see orc_cell_keys_f32): a
+    restatement of the precision the GPU takes this integer decision in, not
+    a definition of the method; cell_keys_f64 is the definition it must agree
+    with away from cell boundaries."""
     xy = np.ascontiguousarray(xy_f32, dtype=np.float32)
     stride = xy.shape[1]
     keys = np.zeros(xy.shape[0], dtype=np.int32)
@@ -308,7 +320,10 @@ def cell_keys_f32(p: Params, xy_f32, anchor):
 
 def neighbor_counts_f32(p: Params, xy_f32, gB, body, query=None):
     """FP32 neighbour counts (n_ff, n_fg2, n_fg1) of the particles in
-    ``query`` (indices; all if None), brute force over all particles."""
+    ``query`` (indices; all if None), brute force over all particles.  This
+    restates the kernels' FP32 predicate (their convention for the integer
+    decision); the definition it must agree with, except on pairs within the
+    band around the support, is neighbor_counts_f64."""
     xy = np.ascontiguousarray(xy_f32, dtype=np.float32)
     gB = np.ascontiguousarray(gB, dtype=np.float64).reshape(-1, 2)
     body = np.ascontiguousarray(body, dtype=np.float64)
@@ -320,6 +335,74 @@ def neighbor_counts_f32(p: Params, xy_f32, gB, body, query=None):
     lib().orc_neighbor_counts_f32(C.byref(p), xy.shape[0], _f(xy), xy.shape[1], gB.shape[0], _d(gB), _d(body), n,
                                   None if q is None else _i(q), _i(nff), _i(nfg2), _i(nfg1))
     return nff, nfg2, nfg1
+
+
+def cell_keys_f64(p: Params, xy_f32, anchor):
+    """Cell keys of SURVEY C13's FP64 definition: floor((x - (anchor - W)) / s)
+    in FP64 on the FP32 positions, clamped to the grid; also returns, per
+    particle, whether a coordinate lies within 2^-20 s of a cell boundary
+    (where the FP32 convention may take the other cell)."""
+    s_, W, G = grid_dims(p)
+    xy = np.asarray(xy_f32, dtype=np.float32)[:, :2].astype(np.float64)
+    t = (xy - (np.asarray(anchor, dtype=np.float64) - W)) / s_
+    c = np.clip(np.floor(t), 0, G - 1).astype(np.int64)
+    near = np.any(np.abs(t - np.round(t)) <= 2.0 ** -20 * np.maximum(np.abs(t), 1.0), axis=1)
+    return (c[:, 1] * G + c[:, 0]).astype(np.int32), near
+
+
+def neighbor_counts_f64(p: Params, xy_f32, gB, body, query=None, band=2.0 ** -20):
+    """Neighbour counts with the FP64 predicate on the FP32 positions
+    (SURVEY C13): returns (n_ff, n_fg2, n_fg1) and their band counts (pairs
+    with |r^2 - s^2| <= band s^2), each an int array over ``query``."""
+    xy = np.ascontiguousarray(xy_f32, dtype=np.float32)
+    gB = np.ascontiguousarray(gB, dtype=np.float64).reshape(-1, 2)
+    body = np.ascontiguousarray(body, dtype=np.float64)
+    q = None if query is None else np.ascontiguousarray(query, dtype=np.int32)
+    n = xy.shape[0] if q is None else q.shape[0]
+    out = np.zeros((n, 6), dtype=np.int32)
+    lib().orc_neighbor_counts_f64(C.byref(p), xy.shape[0], _f(xy), xy.shape[1], gB.shape[0], _d(gB), _d(body), n,
+                                  None if q is None else _i(q), float(band), _i(out))
+    return (out[:, 0], out[:, 2], out[:, 4]), (out[:, 1], out[:, 3], out[:, 5])
+
+
+def switch_counts(p: Params, x, v, gB, body):
+    """Per particle [n_ff(2h), n_fg(2h), n_fg(h), approaching n_fg(h)]: the
+    discrete switches of Algorithm 1 (see orc_switch_counts)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    gB = np.ascontiguousarray(gB, dtype=np.float64).reshape(-1, 2)
+    body = np.ascontiguousarray(body, dtype=np.float64)
+    out = np.zeros((x.shape[0], 4), dtype=np.int32)
+    if lib().orc_switch_counts(C.byref(p), x.shape[0], _d(x), _d(v), gB.shape[0], _d(gB), _d(body), _i(out)):
+        raise MemoryError("oracle switch counts failed")
+    return out
+
+
+def switches_cross(p: Params, gB, states, us):
+    """Where the trajectories started from ``states`` (a list of (x, v, body)
+    triples, e.g. the two ends of a central difference) under the inputs
+    ``us`` (one [K, 3] array per state) take a discrete switch of Algorithm 1
+    differently, over the K steps.  Returns a dict: 'support' the number of
+    (step, particle) cases whose neighbour counts differ (a pair crossed the
+    support of Eq. 22 or 23, where the kernels vanish with two continuous
+    derivatives), 'clip' the cases whose count of approaching ghost pairs
+    differs (a pair crossed the kink of Eq. 18's min(., 0)), and 'first' the
+    first step of either (-1: none)."""
+    cur = [(np.array(a, dtype=np.float64), np.array(b, dtype=np.float64), np.array(c, dtype=np.float64))
+           for a, b, c in states]
+    out = {"support": 0, "clip": 0, "first": -1}
+    K = len(us[0])
+    for k in range(K):
+        counts = [switch_counts(p, a, b, gB, c) for a, b, c in cur]
+        for c in counts[1:]:
+            ns = int(np.any(c[:, :3] != counts[0][:, :3], axis=1).sum())
+            nc = int((c[:, 3] != counts[0][:, 3]).sum())
+            out["support"] += ns
+            out["clip"] += nc
+            if (ns or nc) and out["first"] < 0:
+                out["first"] = k
+        cur = [run(p, a, b, gB, c, 1, u=u[k:k + 1], record=False)[:3] for (a, b, c), u in zip(cur, us)]
+    return out
 
 
 def pair_count(p: Params, x, gB, body) -> int:

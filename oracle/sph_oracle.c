@@ -46,6 +46,9 @@
  *     s_g = ghost_spacing * dx (Table 2's single layer: 0.9 dx).
  *  R10 The "continuity sum" is the time derivative of Eq. 14 along the
  *     kinematic motion: m sum_f v_if . grad W + gamma1 m sum_g v_ig . grad W.
+ *  R34 Eq. 16 takes P_i as printed by default; ghost_pressure_clamp = 1 takes
+ *     max(P_i, 0), so that a particle under tension is not pulled into the
+ *     wall (the paper is silent on the sign of P_i there).
  */
 #include <math.h>
 #include <stdint.h>
@@ -85,6 +88,7 @@ typedef struct {
     int32_t n_rings;     /* number of ghost rings                           */
     int32_t outer_every; /* inner steps per sampling period T_s             */
     double ghost_spacing; /* ghost spacing over dx (Table 2: 0.9); <= 0: 1  */
+    int32_t ghost_pressure_clamp; /* 1: Eq. 16 with max(P_i, 0) (reading R34) */
 } orc_params;
 
 #define ORC_NY 11 /* r_x r_y theta v_x v_y omega F_x F_y T c_x c_y */
@@ -381,11 +385,17 @@ static int brute_query(int n, const double* xy, double x, double y, double radiu
  *   drho      continuity sum (reading R10), [nf], optional
  *   fb        [F_x, F_y, T]: fluid force and torque on the body, Eq. 20
  *   body_acc  [rddot_x, rddot_y, thetaddot], Eq. 20 with u added
+ *   fb_abs    [6], optional: scales of the terms that make up fb, summed over
+ *             the fluid-ghost pairs (Eqs. 16-20) as magnitudes:
+ *             [0..2] sum |f_x|, sum |f_y|, sum |arm x f| of the pair forces;
+ *             [3..5] the same for rho_i df/drho_i (the change of each pair
+ *             force under a relative change of its particle's density, which
+ *             Eq. 11 amplifies by rho / (rho - rho0)).
  * Returns 0, or -1 on allocation failure.
  */
 int orc_eval(const orc_params* p, int nf, const double* x, const double* v, int ng, const double* gB,
              const double* body, const double* u, int brute, double* rho, double* P, double* acc,
-             double* drho, double* fb, double* body_acc)
+             double* drho, double* fb, double* body_acc, double* fb_abs)
 {
     const double h = orc_h(p), m = orc_mass(p), sig = orc_sigma(p);
     const double H2 = 2.0 * h; /* cubic support */
@@ -393,8 +403,9 @@ int orc_eval(const orc_params* p, int nf, const double* x, const double* v, int 
     double* gv = (double*)malloc(sizeof(double) * 2 * (ng > 0 ? ng : 1));
     double* arm = (double*)malloc(sizeof(double) * 2 * (ng > 0 ? ng : 1));
     double* fbi = (double*)calloc(3 * (size_t)(nf > 0 ? nf : 1), sizeof(double));
-    if (!gw || !gv || !arm || !fbi) {
-        free(gw), free(gv), free(arm), free(fbi);
+    double* fba = (double*)calloc(6 * (size_t)(nf > 0 ? nf : 1), sizeof(double));
+    if (!gw || !gv || !arm || !fbi || !fba) {
+        free(gw), free(gv), free(arm), free(fbi), free(fba);
         return -1;
     }
     orc_ghost_world(ng, gB, body, gw, gv, arm); /* Algorithm 1, ghost loop */
@@ -475,14 +486,17 @@ int orc_eval(const orc_params* p, int nf, const double* x, const double* v, int 
             }
             c = brute ? brute_query(ng, gw, xi, yi, h, nb) : bucket_query(&bg, gw, xi, yi, h, nb);
             double fx_b = 0.0, fy_b = 0.0, t_b = 0.0;
+            double sa[6] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
             for (int t = 0; t < c; ++t) {
                 int g = nb[t];
                 double rx = xi - gw[2 * g], ry = yi - gw[2 * g + 1];
                 double r2 = rx * rx + ry * ry, r = sqrt(r2);
                 if (r <= 0.0) continue;
                 double gradWs = orc_dw_spiky(r, h) / r;
-                /* Eq. 16 with the sign of reading R6 (g2f pressure) */
-                double fp = p->ghost_pressure_sign * 2.0 * m * m * Pi_r2 * gradWs;
+                /* Eq. 16 with the sign of reading R6 (g2f pressure); reading
+                 * R34 optionally clamps P_i at zero (the wall only pushes) */
+                double qg = p->ghost_pressure_clamp ? fmax(Pi_r2, 0.0) : Pi_r2;
+                double fp = p->ghost_pressure_sign * 2.0 * m * m * qg * gradWs;
                 /* Eq. 18 with rho_g = rho_i (g2f viscosity) */
                 double vdotr = (vxi - gv[2 * g]) * rx + (vyi - gv[2 * g + 1]) * ry;
                 double fv = m * m * 2.0 * p->beta / (rho[i] + rho[i]) * fmin(vdotr, 0.0) / (r2 + p->eps * h * h) * gradWs;
@@ -493,7 +507,18 @@ int orc_eval(const orc_params* p, int nf, const double* x, const double* v, int 
                 fx_b -= fx;
                 fy_b -= fy;
                 t_b -= arm[2 * g] * fy - arm[2 * g + 1] * fx;
+                /* magnitudes: the pair force, and rho_i d/drho_i of it (Eq. 11:
+                 * rho d(P/rho^2)/drho = k/rho - 2P/rho^2; Eq. 18: -f_v) */
+                double dp = (qg == Pi_r2) ? p->ghost_pressure_sign * 2.0 * m * m * (p->k / rho[i] - 2.0 * Pi_r2) * gradWs : 0.0;
+                double dx_ = (dp - fv) * rx, dy_ = (dp - fv) * ry;
+                sa[0] += fabs(fx);
+                sa[1] += fabs(fy);
+                sa[2] += fabs(arm[2 * g] * fy - arm[2 * g + 1] * fx);
+                sa[3] += fabs(dx_);
+                sa[4] += fabs(dy_);
+                sa[5] += fabs(arm[2 * g] * dy_ - arm[2 * g + 1] * dx_);
             }
+            for (int q = 0; q < 6; ++q) fba[6 * i + q] = sa[q];
             acc[2 * i] = ax + p->grav_x; /* F^external = m g */
             acc[2 * i + 1] = ay + p->grav_y;
             fbi[3 * i] = fx_b;
@@ -513,6 +538,11 @@ int orc_eval(const orc_params* p, int nf, const double* x, const double* v, int 
         fb[1] = Fy;
         fb[2] = T;
     }
+    if (fb_abs) {
+        for (int q = 0; q < 6; ++q) fb_abs[q] = 0.0;
+        for (int i = 0; i < nf; ++i)
+            for (int q = 0; q < 6; ++q) fb_abs[q] += fba[6 * i + q];
+    }
     if (body_acc) { /* Eq. 20 */
         body_acc[0] = (Fx + u[0]) / p->m_body;
         body_acc[1] = (Fy + u[1]) / p->m_body;
@@ -522,7 +552,7 @@ int orc_eval(const orc_params* p, int nf, const double* x, const double* v, int 
         bucket_free(&bf);
         bucket_free(&bg);
     }
-    free(gw), free(gv), free(arm), free(fbi);
+    free(gw), free(gv), free(arm), free(fbi), free(fba);
     return fail ? -1 : 0;
 }
 
@@ -585,7 +615,7 @@ int orc_run(const orc_params* p, int nf, double* x, double* v, int ng, const dou
         }
         double uu[3] = {u ? u[3 * n] : 0.0, u ? u[3 * n + 1] : 0.0, (u ? u[3 * n + 2] : 0.0) + tau_c};
         double fb[3], ba[3];
-        if (orc_eval(p, nf, x, v, ng, gB, body, uu, brute, rho, P, acc, NULL, fb, ba)) {
+        if (orc_eval(p, nf, x, v, ng, gB, body, uu, brute, rho, P, acc, NULL, fb, ba, NULL)) {
             rc = -1;
             break;
         }
@@ -719,6 +749,108 @@ int orc_neighbor_counts_f32(const orc_params* p, int nf, const float* xy, int st
     }
     free(gw);
     return 0;
+}
+
+/*
+ * Neighbour counts with the FP64 predicate r^2 < (2h)^2 (and r^2 < h^2) on
+ * the FP32 inputs: the particle positions are the FP32 numbers given, taken
+ * exactly into FP64; the ghosts are their FP64 world positions (Eq. 21).  The
+ * differences of FP32 numbers are exact in FP64, so only the final sum of
+ * squares rounds.  For each count the band count is the number of pairs with
+ * |r^2 - s^2| <= band * s^2 (s the support): pairs so close to the support
+ * boundary that a predicate evaluated in a lower precision may decide them
+ * either way, where W and grad W vanish continuously.
+ *   out[q][0..5] = n_ff, band_ff, n_fg2, band_fg2, n_fg1, band_fg1
+ * for the particles listed in qidx[nq] (all particles if qidx is NULL).
+ */
+int orc_neighbor_counts_f64(const orc_params* p, int nf, const float* xy, int stride, int ng, const double* gB,
+                            const double* body, int nq, const int32_t* qidx, double band, int32_t* out)
+{
+    const double h = orc_h(p);
+    const double S2 = (2.0 * h) * (2.0 * h), H2 = h * h;
+    double* gw = (double*)malloc(sizeof(double) * 2 * (ng > 0 ? ng : 1));
+    if (!gw) return -1;
+    orc_ghost_world(ng, gB, body, gw, NULL, NULL);
+    if (!qidx) nq = nf;
+#pragma omp parallel for schedule(static)
+    for (int q = 0; q < nq; ++q) {
+        int i = qidx ? qidx[q] : q;
+        double xi = (double)xy[(size_t)stride * i], yi = (double)xy[(size_t)stride * i + 1];
+        int n = 0, nb = 0;
+        for (int j = 0; j < nf; ++j) {
+            if (j == i) continue;
+            double ddx = xi - (double)xy[(size_t)stride * j], ddy = yi - (double)xy[(size_t)stride * j + 1];
+            double r2 = ddx * ddx + ddy * ddy;
+            n += r2 < S2;
+            nb += fabs(r2 - S2) <= band * S2;
+        }
+        int n2 = 0, b2 = 0, n1 = 0, b1 = 0;
+        for (int g = 0; g < ng; ++g) {
+            double ddx = xi - gw[2 * g], ddy = yi - gw[2 * g + 1];
+            double r2 = ddx * ddx + ddy * ddy;
+            n2 += r2 < S2;
+            b2 += fabs(r2 - S2) <= band * S2;
+            n1 += r2 < H2;
+            b1 += fabs(r2 - H2) <= band * H2;
+        }
+        int32_t* o = out + 6 * (size_t)q;
+        o[0] = n, o[1] = nb, o[2] = n2, o[3] = b2, o[4] = n1, o[5] = b1;
+    }
+    free(gw);
+    return 0;
+}
+
+/*
+ * The discrete switches of Algorithm 1 for one state (FP64): per fluid
+ * particle i,
+ *   out[i][0]  #{ j != i : r_ij < 2h }            (Eqs. 10, 12, 14)
+ *   out[i][1]  #{ g : r_ig < 2h }                 (Eq. 14)
+ *   out[i][2]  #{ g : r_ig < h }                  (Eqs. 16, 18)
+ *   out[i][3]  #{ g : r_ig < h, v_ig . r_ig < 0 } (the min(., 0) of Eq. 18)
+ * Two states whose counts agree for every particle take every switch the
+ * same way, so the step map is smooth between them; where they differ, a
+ * pair crossed a support or the viscosity clip.
+ */
+int orc_switch_counts(const orc_params* p, int nf, const double* x, const double* v, int ng, const double* gB,
+                      const double* body, int32_t* out)
+{
+    const double h = orc_h(p);
+    double* gw = (double*)malloc(sizeof(double) * 2 * (ng > 0 ? ng : 1));
+    double* gv = (double*)malloc(sizeof(double) * 2 * (ng > 0 ? ng : 1));
+    if (!gw || !gv) {
+        free(gw), free(gv);
+        return -1;
+    }
+    orc_ghost_world(ng, gB, body, gw, gv, NULL);
+    bucket_t bf, bg;
+    if (bucket_build(&bf, nf, x, 2.0 * h) || bucket_build(&bg, ng, gw, 2.0 * h)) return -1;
+    int fail = 0;
+#pragma omp parallel
+    {
+        int* nb = (int*)malloc(sizeof(int) * (nf + ng + 1));
+        if (!nb) fail = 1;
+#pragma omp for schedule(static)
+        for (int i = 0; i < nf; ++i) {
+            if (!nb) continue;
+            const double xi = x[2 * i], yi = x[2 * i + 1];
+            int32_t* o = out + 4 * (size_t)i;
+            o[0] = bucket_query(&bf, x, xi, yi, 2.0 * h, nb) - 1; /* the particle itself is in its own list */
+            o[1] = bucket_query(&bg, gw, xi, yi, 2.0 * h, nb);
+            int c = bucket_query(&bg, gw, xi, yi, h, nb), app = 0;
+            for (int t = 0; t < c; ++t) {
+                int g = nb[t];
+                double vr = (v[2 * i] - gv[2 * g]) * (xi - gw[2 * g]) + (v[2 * i + 1] - gv[2 * g + 1]) * (yi - gw[2 * g + 1]);
+                app += vr < 0.0;
+            }
+            o[2] = c;
+            o[3] = app;
+        }
+        free(nb);
+    }
+    bucket_free(&bf);
+    bucket_free(&bg);
+    free(gw), free(gv);
+    return fail ? -1 : 0;
 }
 
 /*

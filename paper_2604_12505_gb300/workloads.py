@@ -36,6 +36,7 @@ BASE = dict(
     n_rings=3,
     outer_every=10,
     ghost_spacing=1.0,        # ghosts spaced like the fluid lattice
+    ghost_pressure_clamp=0,   # Eq. 16 with P_i as printed (1: max(P_i, 0))
 )
 
 # Small tank: R = 0.5 m, 50 % fill, dx = 0.02 m (938 fluid + 500 ghosts).

@@ -78,3 +78,31 @@ def test_gamma1_falls_as_ghost_rows_are_added(orc):
     # seen from the first fluid row (dx/2 inside the wall) the third ghost row
     # lies 3 dx away, beyond the support 2h = 2.6 dx: it changes nothing
     assert g[3] == g[2] == g[1]
+
+
+@pytest.mark.parametrize("sign", [-1.0, 1.0])
+def test_ghost_pressure_clamp_reading(orc, sign):
+    # Reading R34: with ghost_pressure_clamp = 1 Eq. 16 takes max(P_i, 0).  A
+    # lone particle next to one ghost has rho_i = m (W(0) + gamma1 W(r)), far
+    # below rho0, so P_i < 0: as printed (clamp 0) the wall term pulls it
+    # towards the ghost for the repulsive sign (-1); clamped, the wall exerts
+    # no pressure force at all, and at P_i > 0 the clamp changes nothing.
+    base = dict(W.BASE, dx=0.01, beta=0.0, ghost_pressure_sign=sign)
+    gB = np.array([[0.2, 0.0]])
+    h = orc.h_of(orc.params(**base))
+    x = np.array([[0.2 - 0.6 * h, 0.0]])
+    v = np.zeros((1, 2))
+    free = orc.evaluate(orc.params(**base), x, v, gB, np.zeros(6))
+    clamped = orc.evaluate(orc.params(**dict(base, ghost_pressure_clamp=1)), x, v, gB, np.zeros(6))
+    assert free["P"][0] < 0
+    towards = (gB[0] - x[0]) @ free["acc"][0]
+    assert (towards > 0) if sign < 0 else (towards < 0)
+    np.testing.assert_array_equal(clamped["acc"], 0.0)
+    np.testing.assert_array_equal(clamped["fb"], 0.0)
+    # a heavy ghost weight compresses the particle (rho_i / rho0 = dx^2 (W(0) +
+    # gamma1 W(r)) is 3.6 at gamma1 = 20): P_i > 0, and the clamp is the identity
+    hi = dict(base, gamma1=20.0)
+    a = orc.evaluate(orc.params(**hi), x, v, gB, np.zeros(6))
+    b = orc.evaluate(orc.params(**dict(hi, ghost_pressure_clamp=1)), x, v, gB, np.zeros(6))
+    assert a["P"][0] > 0
+    np.testing.assert_array_equal(a["acc"], b["acc"])

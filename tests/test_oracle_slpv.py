@@ -188,3 +188,39 @@ def test_closed_loop_equals_the_free_run_under_the_inputs_it_applied():
     e, yh = S.augment(th, u, NX, NY, Ts)
     np.testing.assert_allclose(out[:, 3:], yh * sy, rtol=0, atol=1e-12)
     np.testing.assert_allclose(out[:, :3], e * sy, rtol=0, atol=1e-12)
+
+
+def test_scheduling_network_equals_an_independent_tanh_network():
+    """eta is the two-hidden-layer tanh network of Section 5.3.2 on z = [x, u]:
+    evaluated by torch.nn layers (Linear, Tanh, Linear, Tanh, Linear) loaded
+    with the same weights, at the states and inputs of a free run."""
+    torch = pytest.importorskip("torch")
+    th = _random_theta(7, scale_m1=0.3)
+    P = S.unpack(th, NX, NU, NY)
+    net = torch.nn.Sequential(torch.nn.Linear(NX + NU, 4), torch.nn.Tanh(), torch.nn.Linear(4, 4), torch.nn.Tanh(),
+                              torch.nn.Linear(4, 1)).double()
+    with torch.no_grad():
+        net[0].weight.copy_(torch.tensor(P["W1"]))
+        net[0].bias.copy_(torch.tensor(P["b1"]))
+        net[2].weight.copy_(torch.tensor(P["W2"]))
+        net[2].bias.copy_(torch.tensor(P["b2"]))
+        net[4].weight.copy_(torch.tensor(P["w3"][None, :]))
+        net[4].bias.copy_(torch.tensor(P["b3"]))
+    u = np.random.default_rng(8).normal(size=(30, NU))
+    _, xs, ps = S.simulate(th, u, NX, NY)
+    z = np.concatenate([xs[:-1], u], axis=1)                 # z_k = [x_k; u_k]
+    with torch.no_grad():
+        ref = net(torch.tensor(z)).numpy()[:, 0]
+    np.testing.assert_allclose(ps, ref, rtol=0, atol=1e-14)
+    assert np.ptp(ps) > 0.1                                   # the network is not at a constant
+    # a hand-worked case: one active neuron per layer
+    Q = {k: np.zeros_like(v) for k, v in P.items()}
+    Q["W1"][0, 1] = 2.0
+    Q["b1"][0] = 0.5
+    Q["W2"][0, 0] = -1.5
+    Q["w3"][0] = 3.0
+    Q["b3"][0] = 0.25
+    z1 = np.zeros(NX + NU)
+    z1[1] = 0.4
+    p1, _, _ = S.eta(Q, z1)
+    assert p1 == pytest.approx(3.0 * np.tanh(-1.5 * np.tanh(2.0 * 0.4 + 0.5)) + 0.25, abs=1e-15)
