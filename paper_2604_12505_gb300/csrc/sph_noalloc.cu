@@ -13,11 +13,16 @@
 // it keeps the previous call's contents, so each call clears what must start
 // at zero; two calls that overlap on the GPU (different streams, or the same
 // call from two threads) race on it and must not be issued.
+//
+// A symbol's device address belongs to a CUDA context, not to a device
+// number: a caller may make its own driver-API context current on a device,
+// or reset the primary context.  So every call looks the address up again in
+// the context that is current (cudaGetSymbolAddress allocates nothing) and
+// never reuses an address from an earlier call.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
-#include <mutex>
 
 #include "../../include/sph.h"
 
@@ -134,9 +139,6 @@ __global__ void density_kernel(const Scratch* __restrict__ s, Geo g, const float
     rho[i] = g.m * g.cW * (sf + g.gamma1 * sg);
 }
 
-std::mutex g_mu;
-Scratch* g_addr[64] = {nullptr};   // device address of g_scratch, per device ordinal
-
 }  // namespace sph_noalloc
 
 using namespace sph_noalloc;
@@ -162,21 +164,15 @@ extern "C" int sph_density_noalloc(const sph_params* p, const float* xv, int32_t
         return set_last_error(SPH_E_UNSUPPORTED, "sph_density_noalloc: neighbour grid wider than 256 x 256 cells "
                                                  "(tank radius over dx too large)");
 
-    // set-up, once per device, with that device current
+    // the array's device address in the context current on this call (its
+    // host-side name is only a stand-in and must never reach a kernel)
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
+    if (cudaGetDevice(&dev) != cudaSuccess)
         return set_last_error(SPH_E_CUDA, "sph_density_noalloc: no current CUDA device");
-    Scratch* s = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_addr[dev]) {
-            void* ptr = nullptr;
-            if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr)
-                return set_last_error(SPH_E_CUDA, "sph_density_noalloc: cudaGetSymbolAddress failed");
-            g_addr[dev] = (Scratch*)ptr;
-        }
-        s = g_addr[dev];
-    }
+    void* ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_scratch) != cudaSuccess || !ptr)
+        return set_last_error(SPH_E_CUDA, "sph_density_noalloc: cudaGetSymbolAddress failed");
+    Scratch* s = (Scratch*)ptr;
     if (n_fluid == 0) return SPH_OK;
 
     const double sigma = p->sigma_cubic > 0 ? p->sigma_cubic : 5.0 / (14.0 * 3.14159265358979323846);

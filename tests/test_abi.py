@@ -58,3 +58,16 @@ def test_argument_checks_answer_without_a_gpu():
     g = C.c_double()
     assert lib.sph_gamma1_estimate(C.byref(p), C.byref(g)) == -1
     assert lib.sph_gamma1_estimate(None, C.byref(g)) == -1
+    # the no-allocation density call rejects sizes beyond its fixed array
+    # before any device work (host buffers stand in for the device pointers
+    # and are never dereferenced)
+    lib.sph_density_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32, C.c_void_p,
+                                        C.c_void_p, C.c_void_p]
+    lib.sph_last_error.restype = C.c_char_p
+    q = SphParams(R=0.5, dx=0.02, h_over_dx=1.3, n_rings=3, rho0=1000.0)
+    buf = (C.c_double * 8)()
+    ptr = C.cast(buf, C.c_void_p)
+    assert lib.sph_density_noalloc(C.byref(q), ptr, 4, ptr, 16385, ptr, ptr, None) == -6
+    assert b"16384" in lib.sph_last_error()
+    assert lib.sph_density_noalloc(C.byref(q), ptr, -1, ptr, 0, ptr, ptr, None) == -1
+    assert lib.sph_density_noalloc(C.byref(q), None, 4, ptr, 0, ptr, ptr, None) == -1

@@ -2,8 +2,10 @@
 
 It exists for callers that cannot call cudaMalloc (memory fixed before start,
 or a host application that owns all device memory).  It must give the same
-density as sph_eval, within the density tolerance of the other GPU tests
-(max relative error 1e-5), on consecutive calls that reuse its fixed array.
+density as sph_eval and as the FP64 oracle, within the density tolerance of
+the other GPU tests (max relative error 1e-5), on consecutive calls that
+reuse its fixed array, also when a call follows one on a larger tank whose
+counts and slots are still in the array.
 """
 import ctypes as C
 
@@ -16,11 +18,39 @@ from tests.gpu_util import need_gpu, oracle_state
 pytestmark = pytest.mark.gpu
 
 
-def _call(L, p, x, gB, body, rho, stream):
+def _call(L, p, x, gB, body, rho, stream, n_ghost=None):
     bh = (C.c_double * 6)(*[float(b) for b in body])
+    ng = (0 if gB is None else gB.shape[0]) if n_ghost is None else n_ghost
     return L.sph_density_noalloc(C.byref(p), C.c_void_p(x.data_ptr()), x.shape[0],
                                  C.c_void_p(gB.data_ptr()) if gB is not None else None,
-                                 0 if gB is None else gB.shape[0], bh, C.c_void_p(rho.data_ptr()), C.c_void_p(stream))
+                                 ng, bh, C.c_void_p(rho.data_ptr()), C.c_void_p(stream))
+
+
+def _case(torch, orc, cfg, pos, vel, body, seed):
+    """Device inputs, the sph_eval density and the oracle density of one state."""
+    from paper_2604_12505_gb300.sph import Sim
+    xv, x, v, gB, p = oracle_state(orc, cfg, pos, vel, seed=seed)
+    body = np.array(body, dtype=np.float64)
+    with Sim(cfg) as s:
+        s.set_state(xv, body)
+        ref = s.eval()["rho"].cpu().numpy()
+        gBd = torch.tensor(s.ghosts_body(0), dtype=torch.float64, device="cuda")
+    oref = orc.evaluate(p, x, v, gB, body)["rho"]
+    return torch.tensor(xv, device="cuda"), gBd, body, ref, oref
+
+
+def _run(torch, L, cfg, x, gB, body):
+    from paper_2604_12505_gb300.sph import make_params
+    rho = torch.full((x.shape[0],), float("nan"), dtype=torch.float32, device="cuda")
+    rc = _call(L, make_params(cfg), x, gB, body, rho, torch.cuda.current_stream().cuda_stream)
+    assert rc == 0, L.sph_last_error()
+    got = rho.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    return got
+
+
+def _rel(a, b):
+    return np.abs(a - b).max() / b.min()
 
 
 @pytest.mark.parametrize("cfg,pos,vel,body", [
@@ -30,24 +60,26 @@ def _call(L, p, x, gB, body, rho, stream):
 def test_noalloc_density_matches_eval_on_two_calls(orc, cfg, pos, vel, body):
     torch = need_gpu()
     from paper_2604_12505_gb300 import _lib
-    from paper_2604_12505_gb300.sph import Sim, make_params
     L = _lib.lib()
-    xv, *_ = oracle_state(orc, cfg, pos, vel, seed=31)
-    body = np.array(body)
-    with Sim(cfg) as s:
-        s.set_state(xv, body)
-        ref = s.eval()["rho"].cpu().numpy()
-        gB = torch.tensor(s.ghosts_body(0), dtype=torch.float64, device="cuda")
-    x = torch.tensor(xv, device="cuda")
-    p = make_params(cfg)
-    stream = torch.cuda.current_stream().cuda_stream
+    x, gB, body, ref, oref = _case(torch, orc, cfg, pos, vel, body, seed=31)
     for _ in range(2):
-        rho = torch.full((x.shape[0],), float("nan"), dtype=torch.float32, device="cuda")
-        rc = _call(L, p, x, gB, body, rho, stream)
-        assert rc == 0, L.sph_last_error()
-        got = rho.cpu().numpy()
-        assert np.all(np.isfinite(got))
-        assert np.abs(got - ref).max() / ref.min() <= 1e-5
+        got = _run(torch, L, cfg, x, gB, body)
+        assert _rel(got, ref) <= 1e-5
+        assert _rel(got, oref) <= 1e-5
+
+
+def test_noalloc_clears_a_larger_previous_call(orc):
+    # A large tank fills many cells and slots of the shared array; the next
+    # call, on a small tank with a shifted and rotated body, must see none of it.
+    torch = need_gpu()
+    from paper_2604_12505_gb300 import _lib
+    L = _lib.lib()
+    xl, gl, bl, refl, _ = _case(torch, orc, W.LARGE, 0.1, 0.0, [0.004, -0.002, 0.3, 0, 0, 0], seed=32)
+    xs, gs, bs, refs, orefs = _case(torch, orc, W.SMALL, 0.2, 0.2, [-0.03, 0.05, -1.1, 0, 0, 0], seed=33)
+    assert _rel(_run(torch, L, W.LARGE, xl, gl, bl), refl) <= 1e-5
+    got = _run(torch, L, W.SMALL, xs, gs, bs)
+    assert _rel(got, refs) <= 1e-5
+    assert _rel(got, orefs) <= 1e-5
 
 
 def test_noalloc_rejects_requests_beyond_its_fixed_array():
@@ -55,8 +87,32 @@ def test_noalloc_rejects_requests_beyond_its_fixed_array():
     from paper_2604_12505_gb300 import _lib
     from paper_2604_12505_gb300.sph import make_params
     L = _lib.lib()
+    stream = torch.cuda.current_stream().cuda_stream
     x = torch.zeros((4, 4), dtype=torch.float32, device="cuda")
     rho = torch.zeros(4, dtype=torch.float32, device="cuda")
-    rc = _call(L, make_params(dict(W.BASE, dx=0.001)), x, None, np.zeros(6), rho, torch.cuda.current_stream().cuda_stream)
-    assert rc == -6
+    assert _call(L, make_params(dict(W.BASE, dx=0.001)), x, None, np.zeros(6), rho, stream) == -6
     assert b"256 x 256" in L.sph_last_error()
+    # one ghost above the limit: rejected before any device work
+    g = torch.zeros((16385, 2), dtype=torch.float64, device="cuda")
+    assert _call(L, make_params(W.SMALL), x, g, np.zeros(6), rho, stream) == -6
+    assert b"16384" in L.sph_last_error()
+
+
+def test_noalloc_reports_a_crowded_cell():
+    # 40 particles packed into one grid cell (capacity 32): SPH_E_DIVERGED,
+    # and the next call on a normal state succeeds again.
+    torch = need_gpu()
+    from paper_2604_12505_gb300 import _lib
+    from paper_2604_12505_gb300.sph import make_params
+    L = _lib.lib()
+    stream = torch.cuda.current_stream().cuda_stream
+    cfg = W.SMALL
+    xv = np.zeros((40, 4), dtype=np.float32)
+    xv[:, 0] = 1e-4 * np.arange(40)
+    x = torch.tensor(xv, device="cuda")
+    rho = torch.zeros(40, dtype=torch.float32, device="cuda")
+    assert _call(L, make_params(cfg), x, None, np.zeros(6), rho, stream) == -4
+    assert b"32 particles" in L.sph_last_error()
+    xv[:, 0] = 0.02 * np.arange(40) - 0.4
+    x = torch.tensor(xv, device="cuda")
+    assert _call(L, make_params(cfg), x, None, np.zeros(6), rho, stream) == 0
