@@ -67,6 +67,10 @@ enum {
  *    5/(14 pi) (Eq. 22 prints 15/(14 pi), whose 2-D integral is 3);
  *  - ghost_pressure_sign = -1 makes the ghost pressure of Eq. 16 repel fluid
  *    at positive pressure; +1 is the literal sign of Algorithm 1;
+ *  - ghost_pressure_clamp = 1 takes Eq. 16 with max(P_i, 0): the wall only
+ *    pushes, and a particle under tension (P_i < 0, which the unclamped
+ *    Eq. 11 gives near a free surface) is not pulled into the ghosts; 0 uses
+ *    P_i as printed;
  *  - the density sum of Eq. 14 includes the particle itself, Eq. 11 is not
  *    clamped, and ghosts enter only Eqs. 14 and 16-19.
  */
@@ -90,6 +94,7 @@ typedef struct sph_params {
     int32_t n_rings;            /* ghost rings (>= 1)                         */
     int32_t outer_every;        /* inner steps per sampling period T_s (>= 1) */
     double ghost_spacing;       /* ghost spacing s_g over dx; <= 0 selects 1  */
+    int32_t ghost_pressure_clamp; /* 1: Eq. 16 with max(P_i, 0); 0: as printed */
 } sph_params;
 
 /*
@@ -344,11 +349,14 @@ int sph_gamma1_estimate(const sph_params* p, double* gamma1);
  * library until the process exits): at most 256 x 256 neighbour-grid cells
  * (set by R / dx), 16384 ghosts and 32 particles per cell.  Larger requests
  * return SPH_E_UNSUPPORTED with a message, and a crowded cell returns
- * SPH_E_DIVERGED.  The first call on a device looks up the array's device
- * address, so make that first call before any stream capture.  Every call
+ * SPH_E_DIVERGED.  Each call looks up the array's device address in the
+ * CUDA context current on the calling thread (this allocates nothing), so a
+ * caller may switch contexts or reset the device between calls.  Every call
  * reuses the same array, so calls must not overlap on the GPU: two calls
  * issued on different streams or from different threads at the same time
- * race.  Blocks until the stream has finished the call.
+ * race.  The call waits for the stream to finish (it reads an overflow flag
+ * back), so it cannot be issued on a stream that is being captured into a
+ * CUDA graph.
  */
 int sph_density_noalloc(const sph_params* p, const float* xv, int32_t n_fluid, const double* gB, int32_t n_ghost,
                         const double* body, float* rho, void* stream);

@@ -43,7 +43,7 @@ class SphParams(C.Structure):
         ("gamma1", C.c_double), ("eps", C.c_double), ("m_body", C.c_double), ("J_body", C.c_double),
         ("dt", C.c_double), ("grav_x", C.c_double), ("grav_y", C.c_double), ("sigma_cubic", C.c_double),
         ("ghost_pressure_sign", C.c_double), ("n_rings", C.c_int32), ("outer_every", C.c_int32),
-        ("ghost_spacing", C.c_double),
+        ("ghost_spacing", C.c_double), ("ghost_pressure_clamp", C.c_int32),
     ]
 
 

@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_force_kernel(SimDe
         for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
             const int e = own_index(t, sm);
             const float4 pi = sm.pv[e];
+            const float2 li = sm.plo[e];
             const float2 ri = sm.rho[e];
             const int id = sm.pid[e];
             const float4 ain = A.in[id];
@@ -157,7 +158,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_force_kernel(SimDe
             float qb = 0.f, rb = 0.f;
             auto pair = [&](int j) {
                 const float4 pj = sm.pv[j];
-                const float dx = __fsub_rn(pi.x, pj.x), dy = __fsub_rn(pi.y, pj.y);
+                const float2 d = sep_ff(pi, li, pj, sm.plo[j]);
+                const float dx = d.x, dy = d.y;
                 const float r2 = dist2(dx, dy);
                 if (!(r2 > 0.f)) return;
                 const float2 rj = sm.rho[j];
@@ -193,15 +195,15 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_force_kernel(SimDe
                 for (int dyc = -1; dyc <= 1; ++dyc) {
                     const int a = sm.start[c + dyc * Sh::SX - 1], zz = sm.start[c + dyc * Sh::SX + 2];
                     for (int j = a; j < zz; ++j) {
-                        const float4 pj = sm.pv[j];
-                        if (j != e && dist2(__fsub_rn(pi.x, pj.x), __fsub_rn(pi.y, pj.y)) < T.R2) pair(j);
+                        const float2 d = sep_ff(pi, li, sm.pv[j], sm.plo[j]);
+                        if (j != e && dist2(d.x, d.y) < T.R2) pair(j);
                     }
                 }
             }
             for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
                 const float4 gp = S.gpos[g];
-                const float dx = __fsub_rn(__fsub_rn(pi.x, gp.x), gp.z);
-                const float dy = __fsub_rn(__fsub_rn(pi.y, gp.y), gp.w);
+                const float2 sg = sep_fg(pi, li, gp);
+                const float dx = sg.x, dy = sg.y;
                 const float r2 = dist2(dx, dy);
                 if (!(r2 < T.h2) || !(r2 > 0.f)) return;
                 const float4 gv = S.gvel[g];                             // (v_g, arm)
@@ -210,7 +212,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_force_kernel(SimDe
                 const float Gs = T.cdS * d * d * inv_r;                  // (dW_s/dr) / r
                 const float Gsp = -T.cdS * d * (T.h + r) * inv_r * inv_r; // dGs/dr
                 const float Cp = T.gp_sign * 2.0f * mm;
-                const float fp = Cp * ri.y * Gs;                         // Eq. 16
+                const float qg = T.gp_clamp ? fmaxf(ri.y, 0.f) : ri.y;   // clamped P_i / rho_i^2
+                const float fp = Cp * qg * Gs;                           // Eq. 16
                 const float ux = pi.z - gv.x, uy = pi.w - gv.y;
                 const float vr = ux * dx + uy * dy;
                 const float C = r2 + T.epsh2;
@@ -221,13 +224,13 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_force_kernel(SimDe
                 const float ex = ai.x * T.inv_m - Fbx, ey = ai.y * T.inv_m - Fby;
                 const float cross = gv.z * dy - gv.w * dx;               // (arm x d)_z
                 const float kap = ex * dx + ey * dy - Tbb * cross;
-                qb += kap * Cp * Gs;
+                if (qg == ri.y) qb += kap * Cp * Gs;
                 rb -= kap * fv / ri.x;
                 const float neg = (vr < 0.f) ? 1.0f : 0.0f;
                 const float kvi = kap * neg * cv * Gs;
                 vbx += kvi * dx;
                 vby += kvi * dy;
-                const float kd = Cp * ri.y * Gsp * inv_r + cv * mv * (Gsp * inv_r - 2.0f * Gs / C);
+                const float kd = Cp * qg * Gsp * inv_r + cv * mv * (Gsp * inv_r - 2.0f * Gs / C);
                 const float dfx = kd * dx + neg * cv * Gs * ux, dfy = kd * dy + neg * cv * Gs * uy;
                 const float dbx = kap * dfx + f * (ex + Tbb * gv.w), dby = kap * dfy + f * (ey - Tbb * gv.z);
                 xbx += dbx;
@@ -272,11 +275,13 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_density_kernel(Sim
         for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
             const int e = own_index(t, sm);
             const float4 pi = sm.pv[e];
+            const float2 li = sm.plo[e];
             const float rbi = srb[e];
             float xbx = 0.f, xby = 0.f;
             auto pair = [&](int j) {
                 const float4 pj = sm.pv[j];
-                const float dx = __fsub_rn(pi.x, pj.x), dy = __fsub_rn(pi.y, pj.y);
+                const float2 d = sep_ff(pi, li, pj, sm.plo[j]);
+                const float dx = d.x, dy = d.y;
                 const float r2 = dist2(dx, dy);
                 if (!(r2 > 0.f)) return;
                 const float inv_r = rsqrtf(r2), r = r2 * inv_r;
@@ -294,15 +299,15 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_density_kernel(Sim
                 for (int dyc = -1; dyc <= 1; ++dyc) {
                     const int a = sm.start[c + dyc * Sh::SX - 1], zz = sm.start[c + dyc * Sh::SX + 2];
                     for (int j = a; j < zz; ++j) {
-                        const float4 pj = sm.pv[j];
-                        if (j != e && dist2(__fsub_rn(pi.x, pj.x), __fsub_rn(pi.y, pj.y)) < T.R2) pair(j);
+                        const float2 d = sep_ff(pi, li, sm.pv[j], sm.plo[j]);
+                        if (j != e && dist2(d.x, d.y) < T.R2) pair(j);
                     }
                 }
             }
             for_ghosts(S, T, pi.x, pi.y, bc, bs, brx, bry, [&](int g) {
                 const float4 gp = S.gpos[g];
-                const float dx = __fsub_rn(__fsub_rn(pi.x, gp.x), gp.z);
-                const float dy = __fsub_rn(__fsub_rn(pi.y, gp.y), gp.w);
+                const float2 d = sep_fg(pi, li, gp);
+                const float dx = d.x, dy = d.y;
                 const float r2 = dist2(dx, dy);
                 if (!(r2 < T.R2) || !(r2 > 0.f)) return;
                 const float4 gv = S.gvel[g];

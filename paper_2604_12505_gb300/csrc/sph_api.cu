@@ -164,6 +164,7 @@ struct sph_sim {
     int* d_part_tank = nullptr;
     double* d_scratch_body = nullptr;
     float* d_scratch_xv = nullptr;
+    float* d_scratch_lo = nullptr;
     long long host_step = 0;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -208,8 +209,10 @@ void free_sim(sph_sim* s)
     cudaFree(s->d_part_tank);
     cudaFree(s->d_scratch_body);
     cudaFree(s->d_scratch_xv);
+    cudaFree(s->d_scratch_lo);
     for (int b = 0; b < 2; ++b) {
         cudaFree(s->S.pv[b]);
+        cudaFree(s->S.lo[b]);
         cudaFree(s->S.pid[b]);
         cudaFree(s->S.count[b]);
     }
@@ -257,6 +260,7 @@ TankDev make_tank_dev(const TankHost& t)
     d.epsh2 = (float)(p.eps * h * h);
     d.dt = (float)p.dt;
     d.gp_sign = (float)p.ghost_pressure_sign;
+    d.gp_clamp = p.ghost_pressure_clamp ? 1 : 0;
     d.grav_x = (float)p.grav_x;
     d.grav_y = (float)p.grav_y;
     d.inv_cell = (float)(1.0 / t.cell);
@@ -366,10 +370,27 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
         tile_dims(code, &TX, &TY);
         for (int b = 0; b < B; ++b) {
             first[code].push_back((int)tiles[code].size());
-            const int G = s->tanks[b].G;
+            const TankHost& th = s->tanks[b];
+            const int G = th.G;
+            // Launch order: tiles that meet the wall band first (their ghost
+            // terms make them the longest, so they should take the first
+            // SM slots), then the interior, then the tiles outside the ghost
+            // rings (empty unless fluid has escaped); row-major within each.
+            const double inner = th.p.R - 3.0 * th.cell;
+            const double outer = th.p.R + ((double)th.p.n_rings + 1.0) * ghost_ds(th.p) + th.cell;
             int local = 0;
-            for (int ty = 0; ty < G; ty += TY)
-                for (int tx = 0; tx < G; tx += TX) tiles[code].push_back(make_int4(b, tx, ty, local++));
+            for (int cls = 0; cls < 3; ++cls)
+                for (int ty = 0; ty < G; ty += TY)
+                    for (int tx = 0; tx < G; tx += TX) {
+                        // nearest and farthest distance of the tile from the tank centre
+                        const double x0 = tx * th.cell - th.W, x1 = (tx + TX) * th.cell - th.W;
+                        const double y0 = ty * th.cell - th.W, y1 = (ty + TY) * th.cell - th.W;
+                        const double nx = std::max(std::max(x0, -x1), 0.0), ny = std::max(std::max(y0, -y1), 0.0);
+                        const double fx = std::max(std::fabs(x0), std::fabs(x1)), fy = std::max(std::fabs(y0), std::fabs(y1));
+                        const double dmin = std::hypot(nx, ny), dmax = std::hypot(fx, fy);
+                        const int c = dmin > outer ? 2 : (dmax < inner ? 1 : 0);
+                        if (c == cls) tiles[code].push_back(make_int4(b, tx, ty, local++));
+                    }
         }
         first[code].push_back((int)tiles[code].size());
         s->n_tiles[code] = (int)tiles[code].size();
@@ -397,8 +418,10 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
     rc |= dalloc(&s->d_part_tank, s->n_f_total);
     rc |= dalloc(&s->d_scratch_body, 6 * (size_t)B);
     rc |= dalloc(&s->d_scratch_xv, 4 * (size_t)s->n_f_total);
+    rc |= dalloc(&s->d_scratch_lo, 4 * (size_t)s->n_f_total);
     for (int b = 0; b < 2; ++b) {
         rc |= dalloc(&s->S.pv[b], nslot);
+        rc |= dalloc(&s->S.lo[b], nslot);
         rc |= dalloc(&s->S.pid[b], nslot);
         rc |= dalloc(&s->S.count[b], s->n_cells_total);
     }
@@ -504,6 +527,26 @@ int ensure_graph(sph_sim* s)
 
 long long ceil_div(long long a, long long b) { return (a + b - 1) / b; }
 
+// The particle state as hi parts xv [N, 4] and low parts lo [N, 4] (NULL: not
+// read back / zero), with the body [B, 6].  The public state calls exchange
+// the hi parts only; the checkpoints of the adjoint and the autotuner's
+// snapshot carry both, so that their restored state is the state they saved.
+int get_state_full(sph_sim* sim, float* xv, float* lo, double* body, cudaStream_t st)
+{
+    const int buf = (int)(sim->host_step & 1);
+    CK(launch_get_state(sim->S, xv, lo, body, sim->n_cells_total, buf, st));
+    return SPH_OK;
+}
+
+int set_state_full(sph_sim* sim, const float* xv, const float* lo, const double* body, cudaStream_t st)
+{
+    const int buf = (int)(sim->host_step & 1);
+    CK(cudaMemsetAsync(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int), st));
+    CK(launch_set_body(sim->S, body, buf, st));
+    CK(launch_bin_flat(sim->S, xv, lo, sim->d_part_tank, sim->n_f_total, buf, st));
+    return SPH_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -546,20 +589,13 @@ int sph_ghosts_body(const sph_sim* sim, int32_t b, double* gB_host)
 int sph_get_state(sph_sim* sim, float* xv, double* body, void* stream)
 {
     if (!sim) return fail(SPH_E_INVAL, "sph_get_state: NULL handle");
-    const int buf = (int)(sim->host_step & 1);
-    CK(launch_get_state(sim->S, xv, body, sim->n_cells_total, buf, (cudaStream_t)stream));
-    return SPH_OK;
+    return get_state_full(sim, xv, nullptr, body, (cudaStream_t)stream);
 }
 
 int sph_set_state(sph_sim* sim, const float* xv, const double* body, void* stream)
 {
     if (!sim || !body || (!xv && sim->n_f_total > 0)) return fail(SPH_E_INVAL, "sph_set_state: NULL argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    const int buf = (int)(sim->host_step & 1);
-    CK(cudaMemsetAsync(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int), st));
-    CK(launch_set_body(sim->S, body, buf, st));
-    CK(launch_bin_flat(sim->S, xv, sim->d_part_tank, sim->n_f_total, buf, st));
-    return SPH_OK;
+    return set_state_full(sim, xv, nullptr, body, (cudaStream_t)stream);
 }
 
 int sph_samples_for(const sph_sim* sim, int32_t n_steps, int32_t* n_samples)
@@ -723,6 +759,7 @@ int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const 
     DevScratch mem;
     float4 *adj0 = nullptr, *adj1 = nullptr;
     float *rhob = nullptr, *fbar = nullptr, *part = nullptr, *ck_xv = nullptr, *seg_xv = nullptr, *fin_xv = nullptr;
+    float *ck_lo = nullptr, *seg_lo = nullptr, *fin_lo = nullptr;
     double *bbar = nullptr, *bpart = nullptr, *ck_b = nullptr, *seg_b = nullptr, *fin_b = nullptr, *us = nullptr;
     const int code = adjoint_tile_code();
     int rc = mem.get(&adj0, N) | mem.get(&adj1, N) | mem.get(&rhob, N) | mem.get(&fbar, 8 * (size_t)B) |
@@ -730,7 +767,8 @@ int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const 
              mem.get(&bpart, 6 * (size_t)B) | mem.get(&ck_xv, nxv * (n_seg ? n_seg : 1)) |
              mem.get(&ck_b, 6 * (size_t)B * (n_seg ? n_seg : 1)) | mem.get(&seg_xv, nxv * C) |
              mem.get(&seg_b, 6 * (size_t)B * C) | mem.get(&fin_xv, nxv) | mem.get(&fin_b, 6 * (size_t)B) |
-             mem.get(&us, 3 * (size_t)B * C);
+             mem.get(&us, 3 * (size_t)B * C) | mem.get(&ck_lo, nxv * (n_seg ? n_seg : 1)) |
+             mem.get(&seg_lo, nxv * C) | mem.get(&fin_lo, nxv);
     if (rc) return SPH_E_NOMEM;
     // adjoint of the final state
     if (xvbar_K) CK(cudaMemcpyAsync(adj0, xvbar_K, nxv * sizeof(float), cudaMemcpyDeviceToDevice, st));
@@ -740,11 +778,11 @@ int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const 
     // forward: a checkpoint every C steps, then the final state
     for (int sgi = 0; sgi < n_seg; ++sgi) {
         const int k0 = sgi * C, n = std::min(C, K - k0);
-        if ((rc = sph_get_state(sim, ck_xv + nxv * sgi, ck_b + 6ll * B * sgi, stream))) return rc;
+        if ((rc = get_state_full(sim, ck_xv + nxv * sgi, ck_lo + nxv * sgi, ck_b + 6ll * B * sgi, st))) return rc;
         if (u) CK(slice_u(us, u, B, K, k0, n, st));
         if ((rc = sph_step(sim, u ? us : nullptr, n, nullptr, nullptr, stream))) return rc;
     }
-    if ((rc = sph_get_state(sim, fin_xv, fin_b, stream))) return rc;
+    if ((rc = get_state_full(sim, fin_xv, fin_lo, fin_b, st))) return rc;
     AdjDev A{};
     A.rhobar = rhob;
     A.bbar = bbar;
@@ -769,9 +807,11 @@ int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const 
         // recompute the states of the segment from its checkpoint
         sim->host_step = step0 + k0;
         CK(launch_set_step(sim->d_run, sim->host_step, st));
-        if ((rc = sph_set_state(sim, ck_xv + nxv * sgi, ck_b + 6ll * B * sgi, stream))) return rc;
+        if ((rc = set_state_full(sim, ck_xv + nxv * sgi, ck_lo + nxv * sgi, ck_b + 6ll * B * sgi, st))) return rc;
         for (int k = k0; k < n1; ++k) {
-            if ((rc = sph_get_state(sim, seg_xv + nxv * (k - k0), seg_b + 6ll * B * (k - k0), stream))) return rc;
+            if ((rc = get_state_full(sim, seg_xv + nxv * (k - k0), seg_lo + nxv * (k - k0), seg_b + 6ll * B * (k - k0),
+                                     st)))
+                return rc;
             if (k + 1 < n1) {
                 if (u) CK(slice_u(us, u, B, K, k, 1, st));
                 if ((rc = sph_step(sim, u ? us : nullptr, 1, nullptr, nullptr, stream))) return rc;
@@ -780,7 +820,9 @@ int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const 
         for (int k = n1 - 1; k >= k0; --k) {
             sim->host_step = step0 + k;
             CK(launch_set_step(sim->d_run, sim->host_step, st));
-            if ((rc = sph_set_state(sim, seg_xv + nxv * (k - k0), seg_b + 6ll * B * (k - k0), stream))) return rc;
+            if ((rc = set_state_full(sim, seg_xv + nxv * (k - k0), seg_lo + nxv * (k - k0), seg_b + 6ll * B * (k - k0),
+                                     st)))
+                return rc;
             const long long g = step0 + k;
             A.k = k;
             A.row = (g % oe == 0) ? (int)(g / oe - (step0 + oe - 1) / oe) : -1;
@@ -795,7 +837,7 @@ int sph_vjp(sph_sim* sim, const double* u, int32_t K, const double* ybar, const 
     // leave the simulator at the final state, as sph_jvp does
     sim->host_step = step0 + K;
     CK(launch_set_step(sim->d_run, sim->host_step, st));
-    if ((rc = sph_set_state(sim, fin_xv, fin_b, stream))) return rc;
+    if ((rc = set_state_full(sim, fin_xv, fin_lo, fin_b, st))) return rc;
     CK(cudaStreamSynchronize(st));  // the scratch buffers are freed on return
     return SPH_OK;
 }
@@ -879,7 +921,7 @@ int sph_autotune(sph_sim* sim, int32_t steps, int32_t* chosen, double* us_per_st
     CK(cudaStreamSynchronize(st));
     CK(cudaMemcpy(body.data(), sim->d_body, sim->B * sizeof(BodyDev), cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(&run, sim->d_run, sizeof(RunDev), cudaMemcpyDeviceToHost));
-    int rc = sph_get_state(sim, sim->d_scratch_xv, nullptr, st);
+    int rc = get_state_full(sim, sim->d_scratch_xv, sim->d_scratch_lo, nullptr, st);
     if (rc) return rc;
     const long long step0 = sim->host_step;
     const int old_tile = sim->tile_code;
@@ -910,7 +952,7 @@ int sph_autotune(sph_sim* sim, int32_t steps, int32_t* chosen, double* us_per_st
         CK(cudaMemcpy(sim->d_run, &run, sizeof(RunDev), cudaMemcpyHostToDevice));
         const int buf = (int)(step0 & 1);
         CK(cudaMemset(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int)));
-        CK(launch_bin_flat(sim->S, sim->d_scratch_xv, sim->d_part_tank, sim->n_f_total, buf, st));
+        CK(launch_bin_flat(sim->S, sim->d_scratch_xv, sim->d_scratch_lo, sim->d_part_tank, sim->n_f_total, buf, st));
         CK(cudaStreamSynchronize(st));
     }
     cudaEventDestroy(e0);

@@ -9,6 +9,12 @@
 //     cell of the other buffer (atomic slot claim), so no sort or scan pass
 //     exists.  Within a cell the kernels order particles by x, then by
 //     index, which makes every neighbour sum deterministic.
+//   * per slot also the low parts (x_lo, y_lo, vx_lo, vy_lo) of the particle
+//     state: the state is carried as two-float (hi + lo) FP32 pairs, so that
+//     the kick and the drift of every step do not round the state to FP32
+//     (at 0.5 m from the origin one FP32 position step is 6e-8 m, close to a
+//     particle's motion in one step of the large tank); separations are
+//     formed from hi and lo, the kernel arithmetic stays FP32.
 //   * per-slot float2 (rho, P / rho^2) written by the density kernel.
 //   * ghosts: body-frame positions (two-float) binned once into a body-frame
 //     grid, and per step the world position as an FP32 (hi, lo) pair plus
@@ -39,6 +45,7 @@ struct TankDev {
     float clip;                   // 2h (1 + 1e-3): a candidate whose x-separation exceeds it lies outside the support
     float hclip;                  // h (1 + 1e-3): likewise for the ghost terms of the force pass (support h)
     float g_cell;                 // fl32(ghost-grid cell side)
+    int gp_clamp;                 // Eq. 16 with max(P_i, 0)
     int G;                        // cells per side (fluid and ghost grid)
     int n_f, n_g;
     int cell_base;                // first cell of this tank in the global grid arrays
@@ -68,9 +75,20 @@ struct BodyDev {
     // tangent (forward-mode derivative) of the body state, FP64, and its FP32 copy
     double tr[2], tth, tv[2], tw;
     float ftr[2], ftth, ftv[2], ftw;
-    unsigned int done;            // reduction groups of this tank finished in the current force pass
+    // fluid force, torque and particle-position sums of the current force
+    // pass as 64-bit fixed point (units of 2^-32, two's complement): the
+    // tiles add them with integer atomics, whose sum does not depend on the
+    // order of the additions, and the tank's last tile reads and clears them
+    unsigned long long acc[5];    // F_x, F_y, T, sum x, sum y
+    unsigned int done;            // tiles (reduction groups in the tangent variant) finished in the current force pass
     int flags;                    // SPH_FLAG_* bits
 };
+
+// Fixed point of the body accumulators: a value v is held as round(v 2^32).
+// A two-float (hi, lo) sum converts term by term; scaling by a power of two
+// is exact, and each conversion rounds once to the nearest unit (2.3e-10).
+constexpr float kFixScale = 4294967296.0f;   // 2^32
+constexpr double kFixUnit = 1.0 / 4294967296.0;
 
 // Two-float (hi + lo) arithmetic on the FP32 pipe (error-free transformations,
 // about 48 significant bits): used for ghost world positions (Eq. 21).
@@ -101,6 +119,31 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b)
     e = fmaf(a.x, b.y, e);
     e = fmaf(a.y, b.x, e);
     return df_norm(p, e);
+}
+
+// TwoSum: s + e = a + b exactly (s = fl(a + b)).
+__device__ __forceinline__ float2 two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return make_float2(s, e);
+}
+
+// Separation (x_i - x_j, y_i - y_j) of two particles held as hi + lo: the hi
+// difference (exact for neighbours: Sterbenz) plus the lo difference, rounded
+// once.  With lo = 0 it is exactly the FP32 difference of the hi parts.
+__device__ __forceinline__ float2 sep_ff(float4 pi, float2 li, float4 pj, float2 lj)
+{
+    return make_float2(__fadd_rn(__fsub_rn(pi.x, pj.x), __fsub_rn(li.x, lj.x)),
+                       __fadd_rn(__fsub_rn(pi.y, pj.y), __fsub_rn(li.y, lj.y)));
+}
+
+// Separation of a particle (hi + lo) from a ghost at gp = (x_hi, y_hi, x_lo, y_lo).
+__device__ __forceinline__ float2 sep_fg(float4 pi, float2 li, float4 gp)
+{
+    return make_float2(__fadd_rn(__fsub_rn(pi.x, gp.x), __fsub_rn(li.x, gp.z)),
+                       __fadd_rn(__fsub_rn(pi.y, gp.y), __fsub_rn(li.y, gp.w)));
 }
 
 struct RunDev {
@@ -169,6 +212,7 @@ struct SimDev {
     BodyDev* body;
     RunDev* run;
     float4* pv[2];
+    float4* lo[2];                // low parts (x_lo, y_lo, vx_lo, vy_lo) of the state in each slot
     int* pid[2];
     int* count[2];
     float2* rhoP;                 // indexed by slot of the current buffer

@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
         const int e = own_index(t, sm);
         const float4 pi = sm.pv[e];
+        const float2 li = sm.plo[e];
         const int c = sm.cell[e];
         float Sf = 0.f, Df = 0.f, dRf = 0.f, dRg = 0.f;
         float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -108,7 +109,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             const int z = lower_x(sm, sm.start[cl + 2], sm.start[cl + 3], xhi);
             for (int j = a; j < z; ++j) {
                 const float4 pj = sm.pv[j];
-                const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);
+                const float2 d = sep_ff(pi, li, pj, sm.plo[j]);
+                const float ddx = d.x, ddy = d.y;
                 const float r2 = dist2(ddx, ddy);
                 const bool in = r2 < T.R2;
                 const float inv_r = rsqrtf(fmaxf(r2, FLT_MIN));
@@ -137,8 +139,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         // one ghost within reach: gp = (x_hi, y_hi, x_lo, y_lo) world position,
         // gv = (v_x, v_y, arm_x, arm_y) (Eq. 21), (tgx, tgy) its position tangent
         auto ghost = [&](const float4 gp, const float4 gv, float tgx, float tgy) {
-            const float ddx = __fsub_rn(__fsub_rn(pi.x, gp.x), gp.z);
-            const float ddy = __fsub_rn(__fsub_rn(pi.y, gp.y), gp.w);
+            const float2 d = sep_fg(pi, li, gp);
+            const float ddx = d.x, ddy = d.y;
             const float r2 = dist2(ddx, ddy);
             if (r2 < T.R2) {
                 ++ng2;
@@ -307,36 +309,66 @@ __device__ Red warp_reduce_partials(const TilePartial* P, int p0, int p1, bool c
 // Body update by the last CTA of a tank (Eq. 20, Eq. 28, outputs)
 // ---------------------------------------------------------------------------
 // Runs in warp 0 of the CTA that finished the tank's reduction, with the
-// reduced partials r (and tr, tangent) valid in lane 0.  The FP64 pipe of this
-// GPU is narrow and every global access on the serial path costs an L2 round
-// trip, so the lanes load the body and input values (finalize_preload) before
-// the partials are reduced, the body is updated in registers and stored once,
-// and the masses enter as reciprocals.
+// reduced fluid force, torque and position sums as FP64 totals.  The FP64 pipe
+// of this GPU is narrow and every global access on the serial path costs an
+// L2 round trip, so warp 0 of every CTA loads the values the update reads
+// (finalize_preload) right after the grid dependency resolves, while the tile
+// is staged; the body is updated in registers and stored once, and the masses
+// enter as reciprocals.
 //
-// finalize_preload: lane l of warp 0 loads one value: the body's r, theta,
-// rdot, thetadot, cos, sin (l < 8, the leading doubles of BodyDev), the held
-// control torque (8), the input (9..11); lane 0 collects them.
-__device__ __forceinline__ double finalize_preload(const SimDev& S, int tank)
+// finalize_preload: lane l of warp 0 holds one value (as a double or as the
+// bits of one): the body's r, theta, rdot, thetadot, cos, sin (l < 8, the
+// leading doubles of BodyDev), the held control torque (8), the input of this
+// step (9..11), the controller's J, omega, xi (12..14), the reference angle of
+// this sample (15), the controller / held-tank switches (16), the sample
+// output pointer (17), the call's first step (18) and the sample stride (19).
+__device__ __forceinline__ double finalize_preload(const SimDev& S, const TankDev& T, int tank)
 {
     const int lane = (int)(threadIdx.x & 31);
     const RunDev* run = S.run;
     const BodyDev* bp = S.body + tank;
-    const long long k = run->step - run->step0;
-    const double* up = run->u;
+    const long long step = run->step, step0 = run->step0;
+    const long long k = step - step0;
     double pre = 0.0;
-    if (lane < 8) pre = reinterpret_cast<const double*>(bp)[lane];
-    else if (lane == 8) pre = bp->tau_c;
-    else if (lane < 12 && up) pre = up[tank * run->u_tank_stride + 3 * k + (lane - 9)];
+    if (lane < 8) {
+        pre = reinterpret_cast<const double*>(bp)[lane];
+    } else if (lane == 8) {
+        pre = bp->tau_c;
+    } else if (lane < 12) {
+        const double* up = run->u;
+        if (up) pre = up[tank * run->u_tank_stride + 3 * k + (lane - 9)];
+    } else if (lane == 12) {
+        pre = run->ctrl_J;
+    } else if (lane == 13) {
+        pre = run->ctrl_w;
+    } else if (lane == 14) {
+        pre = run->ctrl_xi;
+    } else if (lane == 15) {
+        const long long oe = T.outer_every;
+        const double* ref = run->theta_ref;
+        if (ref && (step % oe) == 0) pre = ref[tank * run->ref_stride + (step / oe - (step0 + oe - 1) / oe)];
+    } else if (lane == 16) {
+        pre = __longlong_as_double((long long)(run->ctrl_on ? 1 : 0) | (long long)(run->body_fixed ? 2 : 0));
+    } else if (lane == 17) {
+        pre = __longlong_as_double((long long)run->y);
+    } else if (lane == 18) {
+        pre = __longlong_as_double(step0);
+    } else if (lane == 19) {
+        pre = __longlong_as_double(run->y_tank_stride);
+    }
     return pre;
 }
 
+// Fx, Fy, Tq: fluid force and torque on the body (Eq. 20); Cx, Cy: sums of the
+// particle positions (sample steps only).  add_pairs: pair interactions of the
+// pass still to be added to the tank's count (the tiles of the step pass add
+// theirs themselves).  tr: tangent of the reduced sums (TAN only).
 __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
-                              bool sample, bool tan, const Red& r, const Red& tr, double pre)
+                              long long step, bool sample, bool tan, double Fx, double Fy, double Tq, double Cx,
+                              double Cy, unsigned long long add_pairs, const Red& tr, double pre)
 {
     RunDev* run = S.run;
     BodyDev* bp = S.body + tank;
-    const long long step = run->step, step0 = run->step0;
-    const long long k = step - step0;
     const int lane = (int)(threadIdx.x & 31);
     double rx = __shfl_sync(0xffffffffu, pre, 0), ry = __shfl_sync(0xffffffffu, pre, 1);
     double th = __shfl_sync(0xffffffffu, pre, 2), vx = __shfl_sync(0xffffffffu, pre, 3);
@@ -345,24 +377,27 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
     double tau_c = __shfl_sync(0xffffffffu, pre, 8);
     const double ux = __shfl_sync(0xffffffffu, pre, 9), uy = __shfl_sync(0xffffffffu, pre, 10);
     const double ut = __shfl_sync(0xffffffffu, pre, 11);
+    const double cJ = __shfl_sync(0xffffffffu, pre, 12), cw = __shfl_sync(0xffffffffu, pre, 13);
+    const double cxi = __shfl_sync(0xffffffffu, pre, 14), ref = __shfl_sync(0xffffffffu, pre, 15);
+    const long long sw = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 16));
+    double* const yout = (double*)__double_as_longlong(__shfl_sync(0xffffffffu, pre, 17));
+    const long long step0 = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 18));
+    const long long ystride = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 19));
     if (lane != 0) return;
-    const int ctrl_on = run->ctrl_on, body_fixed = run->body_fixed;
+    const long long k = step - step0;
+    const bool ctrl_on = (sw & 1) != 0, body_fixed = (sw & 2) != 0;
 
-    // FP64 from here on: assembly of the reduced force/torque and the body
-    const double Fx = (double)r.fx.hi + (double)r.fx.lo;
-    const double Fy = (double)r.fy.hi + (double)r.fy.lo;
-    const double Tq = (double)r.t.hi + (double)r.t.lo;
+    // FP64 from here on: assembly of the body state
     if (sample) {
         const long long oe = T.outer_every;
         const long long row = step / oe - (step0 + oe - 1) / oe;
         if (ctrl_on) {  // Eq. 28 under zero-order hold
-            const double ref = run->theta_ref ? run->theta_ref[tank * run->ref_stride + row] : 0.0;
-            const double Jc = run->ctrl_J > 0.0 ? run->ctrl_J : T.J_body;
-            tau_c = Jc * run->ctrl_w * run->ctrl_w * (ref - th) - 2.0 * run->ctrl_xi * Jc * run->ctrl_w * w;
+            const double Jc = cJ > 0.0 ? cJ : T.J_body;
+            tau_c = Jc * cw * cw * (ref - th) - 2.0 * cxi * Jc * cw * w;
             bp->tau_c = tau_c;
         }
-        if (run->y) {
-            double* y = run->y + tank * run->y_tank_stride + row * SPH_NY;
+        if (yout) {
+            double* y = yout + tank * ystride + row * SPH_NY;
             y[0] = rx;
             y[1] = ry;
             y[2] = th;
@@ -372,8 +407,8 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
             y[6] = Fx;
             y[7] = Fy;
             y[8] = Tq;
-            y[9] = T.n_f ? ((double)r.cx.hi + (double)r.cx.lo) / T.n_f : 0.0;
-            y[10] = T.n_f ? ((double)r.cy.hi + (double)r.cy.lo) / T.n_f : 0.0;
+            y[9] = T.n_f ? Cx / T.n_f : 0.0;
+            y[10] = T.n_f ? Cy / T.n_f : 0.0;
         }
     }
     if (tan && !eval) {  // tangent of Eq. 20 and of the kick-then-drift body step
@@ -483,7 +518,7 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
         bp->fry = (float)ry;
         bp->fo_next[0] = (float)(rx - T.W);
         bp->fo_next[1] = (float)(ry - T.W);
-        bp->pairs += r.pairs;
+        bp->pairs += add_pairs;
     }
     bp->done = 0;
     if (S.B == 1) {  // the only tank: its step is the pass's (visible when the kernel completes)
@@ -498,6 +533,13 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
     }
 }
 
+// Adds a two-float sum to a fixed-point body accumulator (an integer
+// reduction: the total does not depend on the order of the tiles).
+__device__ __forceinline__ void fix_add(unsigned long long* a, F2 v)
+{
+    const long long q = __float2ll_rn(v.hi * kFixScale) + __float2ll_rn(v.lo * kFixScale);
+    atomicAdd(a, (unsigned long long)q);
+}
 // ---------------------------------------------------------------------------
 // Force pass: Eqs. 10, 12, 16-19, Algorithm 1, symplectic Euler, re-binning
 // ---------------------------------------------------------------------------
@@ -521,6 +563,10 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     const long long step = S.run->step;
     const int buf = (int)(step & 1), nbuf = buf ^ 1;
     const bool sample = !eval && (step % T.outer_every) == 0;
+    // what the body update reads, in flight while the tile is staged (only
+    // the tank's last tile uses it)
+    double pre = 0.0;
+    if (threadIdx.x < 32) pre = finalize_preload(S, T, tank);
     const float damp = 1.0f - S.run->damping;
 
     const F2 z{0.f, 0.f};
@@ -541,8 +587,10 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
             const int e = own_index(t, sm);
             const float4 pi = sm.pv[e];
+            const float2 li = sm.plo[e];
             const float2 ri = sm.rho[e];
             const int c = sm.cell[e];
+            const float4 lo4 = eval ? make_float4(0.f, 0.f, 0.f, 0.f) : S.lo[buf][sm.slot[e]];  // for the integration
             float ax = 0.f, ay = 0.f, tax = 0.f, tay = 0.f;
             float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
             float2 tri = make_float2(0.f, 0.f);
@@ -554,7 +602,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             // one fluid pair, r < 2h, j != i: Eqs. 10 and 12
             auto pair = [&](int j) {
                 const float4 pj = sm.pv[j];
-                const float ddx = __fsub_rn(pi.x, pj.x), ddy = __fsub_rn(pi.y, pj.y);
+                const float2 d = sep_ff(pi, li, pj, sm.plo[j]);
+                const float ddx = d.x, ddy = d.y;
                 const float r2 = dist2(ddx, ddy);
                 if (r2 > 0.f) {
                     const float2 rj = sm.rho[j];
@@ -595,8 +644,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int a = sm.start[c + dy * Sh::SX - 1], zz = sm.start[c + dy * Sh::SX + 2];
                     for (int j = a; j < zz; ++j) {
-                        const float4 pj = sm.pv[j];
-                        if (j != e && dist2(__fsub_rn(pi.x, pj.x), __fsub_rn(pi.y, pj.y)) < T.R2) {
+                        const float2 d = sep_ff(pi, li, sm.pv[j], sm.plo[j]);
+                        if (j != e && dist2(d.x, d.y) < T.R2) {
                             ++nff;
                             pair(j);
                         }
@@ -604,11 +653,13 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 }
             }
             int nfg = 0;
+            // P_i / rho_i^2 in Eq. 16: clamped at zero when the wall only pushes
+            const float qg = T.gp_clamp ? fmaxf(ri.y, 0.f) : ri.y;
             // one ghost: gp its world position (x_hi, y_hi, x_lo, y_lo), load_gv()
             // its (v_x, v_y, arm_x, arm_y), read only for a pair within reach
             auto ghost = [&](int g, const float4 gp, auto&& load_gv) {
-                const float ddx = __fsub_rn(__fsub_rn(pi.x, gp.x), gp.z);
-                const float ddy = __fsub_rn(__fsub_rn(pi.y, gp.y), gp.w);
+                const float2 d = sep_fg(pi, li, gp);
+                const float ddx = d.x, ddy = d.y;
                 const float r2 = dist2(ddx, ddy);
                 if (r2 < T.h2) {
                     ++nfg;
@@ -618,7 +669,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                         const float r = r2 * inv_r;
                         const float d = T.h - r;
                         const float gWs = T.cdS * d * d * inv_r;                         // (dW_s3/dr)/r
-                        const float fp = T.gp_sign * 2.0f * mm * ri.y * gWs;            // Eq. 16
+                        const float fp = T.gp_sign * 2.0f * mm * qg * gWs;              // Eq. 16
                         const float vr = (pi.z - gv.x) * ddx + (pi.w - gv.y) * ddy;
                         const float fv = __fdividef(mm * T.beta2 * fminf(vr, 0.f), (ri.x + ri.x) * (r2 + T.epsh2)) * gWs;  // Eq. 18
                         const float f = fp + fv;
@@ -633,7 +684,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                             const float tdx = ti.x - tg.x, tdy = ti.y - tg.y;
                             const float rd = ddx * tdx + ddy * tdy;
                             const float tGs = -T.cdS * d * (T.h + r) * inv_r * inv_r * rd * inv_r;  // d(Gs)
-                            const float tfp = T.gp_sign * 2.0f * mm * tri.y;
+                            const float tfp = T.gp_sign * 2.0f * mm * (qg == ri.y ? tri.y : 0.f);
                             float tcv = 0.f;
                             if (vr < 0.f) {
                                 const float Cc = r2 + T.epsh2;
@@ -642,7 +693,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                                 tcv = __fdividef(mm * T.beta2, (ri.x + ri.x) * Cc) *
                                       (tA - vr * (__fdividef(tri.x, ri.x) + __fdividef(2.0f * rd, Cc)));
                             }
-                            const float cf = T.gp_sign * 2.0f * mm * ri.y +               // fp + fv without Gs
+                            const float cf = T.gp_sign * 2.0f * mm * qg +                 // fp + fv without Gs
                                              __fdividef(mm * T.beta2 * fminf(vr, 0.f), (ri.x + ri.x) * (r2 + T.epsh2));
                             const float tf = (tfp + tcv) * gWs + cf * tGs;
                             const float tfx = tf * ddx + f * tdx, tfy = tf * ddy + f * tdy;
@@ -690,9 +741,17 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 }
                 if (E.keys) E.keys[id] = (cy0 - 1 + c / Sh::SX) * T.G + (cx0 - 1 + c % Sh::SX);
             } else {
-                // kick then drift (Section 3.4), then bin into the next grid
-                const float vx = fmaf(T.dt, ax, pi.z) * damp, vy = fmaf(T.dt, ay, pi.w) * damp;
-                const float x = fmaf(T.dt, vx, pi.x), y = fmaf(T.dt, vy, pi.y);
+                // kick then drift (Section 3.4) on the two-float state, then bin
+                // into the next grid: v' = (v + dt a)(1 - c), x' = x + dt v'
+                float2 kx = two_sum(pi.z, fmaf(T.dt, ax, lo4.z)), ky = two_sum(pi.w, fmaf(T.dt, ay, lo4.w));
+                if (damp != 1.0f) {  // relaxation: scale the two-float velocity
+                    const float hx = kx.x * damp, hy = ky.x * damp;
+                    kx = two_sum(hx, fmaf(kx.x, damp, -hx) + kx.y * damp);
+                    ky = two_sum(hy, fmaf(ky.x, damp, -hy) + ky.y * damp);
+                }
+                const float2 dx2 = two_sum(pi.x, fmaf(T.dt, kx.x, fmaf(T.dt, kx.y, lo4.x)));
+                const float2 dy2 = two_sum(pi.y, fmaf(T.dt, ky.x, fmaf(T.dt, ky.y, lo4.y)));
+                const float vx = kx.x, vy = ky.x, x = dx2.x, y = dy2.x;
                 if (!(isfinite(x) && isfinite(y) && isfinite(vx) && isfinite(vy))) flags |= SPH_FLAG_NAN;
                 bool out = false;
                 const int ccx = cell_coord(x, ox, T.inv_cell, T.G, &out);
@@ -702,6 +761,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 const int slot = atomicAdd(&S.count[nbuf][cell], 1);
                 if (slot < kCap) {
                     S.pv[nbuf][cell * kCap + slot] = make_float4(x, y, vx, vy);
+                    S.lo[nbuf][cell * kCap + slot] = make_float4(dx2.y, dy2.y, kx.y, ky.y);
                     S.pid[nbuf][cell * kCap + slot] = id;
                     if constexpr (TAN) {  // tangent of kick then drift, binned with the particle
                         const float tvx = fmaf(T.dt, tax, ti.z) * damp, tvy = fmaf(T.dt, tay, ti.w) * damp;
@@ -727,65 +787,104 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     if (flags) atomicOr(&S.body[tank].flags, flags);
     const bool any_wall = __syncthreads_or(wall) != 0;
     Red r = block_reduce(acc, any_wall, sample, scratch);
-    Red tr = r;
-    if constexpr (TAN) tr = block_reduce(tacc, any_wall, sample, scratch);
-    // fixed-order reduction of the tile partials.  One level when the tank's
-    // last tile can fetch them with at most kOneLevelLoads loads per thread
-    // (every small tank, the large tank at 8x4): the last tile (by a counter
-    // of finished tiles) sums them with the whole block.  Otherwise two
-    // levels: the last tile of each group of kTileGroup tiles sums the group,
-    // the last group of the tank sums the groups.
     const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
-    if (t1 - t0 <= kOneLevelLoads * (int)blockDim.x) {
+    if constexpr (!TAN) {
+        // The tile's sums go into the tank's fixed-point accumulators by
+        // integer atomics (order-independent, so every run, and a tank run
+        // alone or in a batch, gets the same bits); the tank's last tile, by
+        // a counter of finished tiles, reads them and updates the body.
+        BodyDev* bp = S.body + tank;
         if (threadIdx.x == 0) {
-            store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
-            if constexpr (TAN) store_partial(S.tpartials + blockIdx.x, tr, any_wall ? 1 : 0);
+            if (any_wall) {
+                fix_add(&bp->acc[0], r.fx);
+                fix_add(&bp->acc[1], r.fy);
+                fix_add(&bp->acc[2], r.t);
+            }
+            if (sample) {
+                fix_add(&bp->acc[3], r.cx);
+                fix_add(&bp->acc[4], r.cy);
+            }
+            if (!eval && r.pairs) atomicAdd(&bp->pairs, r.pairs);
             fence_acq_rel();
-            is_last = (atomicAdd(&S.body[tank].done, 1u) == (unsigned)(t1 - t0 - 1));
+            is_last = (atomicAdd(&bp->done, 1u) == (unsigned)(t1 - t0 - 1));
         }
         __syncthreads();
-        if (!is_last) return;
+        if (!is_last || threadIdx.x >= 32) return;
         fence_acq_rel();
-        double pre = 0.0;
-        if (threadIdx.x < 32) pre = finalize_preload(S, tank);
-        const Red rt = block_reduce_partials(S.partials, t0, t1, sample, scratch);
-        Red trt = rt;
-        if constexpr (TAN) trt = block_reduce_partials(S.tpartials, t0, t1, sample, scratch);
-        if (threadIdx.x < 32) tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN, rt, trt, pre);
+        const int lane = (int)threadIdx.x;
+        long long q = 0;
+        if (lane < 5) {
+            q = (long long)__ldcg(&bp->acc[lane]);
+            bp->acc[lane] = 0ull;  // cleared for the next pass (every addition of this one is counted)
+        }
+        const double Fx = (double)__shfl_sync(0xffffffffu, q, 0) * kFixUnit;
+        const double Fy = (double)__shfl_sync(0xffffffffu, q, 1) * kFixUnit;
+        const double Tq = (double)__shfl_sync(0xffffffffu, q, 2) * kFixUnit;
+        const double Cx = (double)__shfl_sync(0xffffffffu, q, 3) * kFixUnit;
+        const double Cy = (double)__shfl_sync(0xffffffffu, q, 4) * kFixUnit;
+        tank_finalize(S, T, tank, eval, E, nbuf, step, sample, false, Fx, Fy, Tq, Cx, Cy, 0ull, r, pre);
         return;
-    }
-    const int gi = (blockIdx.x - t0) / kTileGroup;
-    const int gt0 = t0 + gi * kTileGroup, gt1 = min(gt0 + kTileGroup, t1);
-    const int g = S.group_first[tank] + gi;
-    if (threadIdx.x == 0) {
-        store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
-        if constexpr (TAN) store_partial(S.tpartials + blockIdx.x, tr, any_wall ? 1 : 0);
+    } else {
+        // Tangent variant: fixed-order reduction of the tile partials (the
+        // tangent's scale is the caller's, unsuited to a fixed point).  One
+        // level when the tank's last tile can fetch them with at most
+        // kOneLevelLoads loads per thread: the last tile (by a counter of
+        // finished tiles) sums them with the whole block.  Otherwise two
+        // levels: the last tile of each group of kTileGroup tiles sums the
+        // group, the last group of the tank sums the groups.
+        Red tr = block_reduce(tacc, any_wall, sample, scratch);
+        auto finish = [&](const Red& rt, const Red& trt) {
+            tank_finalize(S, T, tank, eval, E, nbuf, step, sample, true, (double)rt.fx.hi + (double)rt.fx.lo,
+                          (double)rt.fy.hi + (double)rt.fy.lo, (double)rt.t.hi + (double)rt.t.lo,
+                          (double)rt.cx.hi + (double)rt.cx.lo, (double)rt.cy.hi + (double)rt.cy.lo, rt.pairs, trt,
+                          pre);
+        };
+        if (t1 - t0 <= kOneLevelLoads * (int)blockDim.x) {
+            if (threadIdx.x == 0) {
+                store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
+                store_partial(S.tpartials + blockIdx.x, tr, any_wall ? 1 : 0);
+                fence_acq_rel();
+                is_last = (atomicAdd(&S.body[tank].done, 1u) == (unsigned)(t1 - t0 - 1));
+            }
+            __syncthreads();
+            if (!is_last) return;
+            fence_acq_rel();
+            const Red rt = block_reduce_partials(S.partials, t0, t1, sample, scratch);
+            const Red trt = block_reduce_partials(S.tpartials, t0, t1, sample, scratch);
+            if (threadIdx.x < 32) finish(rt, trt);
+            return;
+        }
+        const int gi = (blockIdx.x - t0) / kTileGroup;
+        const int gt0 = t0 + gi * kTileGroup, gt1 = min(gt0 + kTileGroup, t1);
+        const int g = S.group_first[tank] + gi;
+        if (threadIdx.x == 0) {
+            store_partial(S.partials + blockIdx.x, r, any_wall ? 1 : 0);
+            store_partial(S.tpartials + blockIdx.x, tr, any_wall ? 1 : 0);
+            fence_acq_rel();
+            is_last = (atomicAdd(&S.gdone[g], 1u) == (unsigned)(gt1 - gt0 - 1));
+        }
+        __syncthreads();
+        if (!is_last || threadIdx.x >= 32) return;  // warp 0 of the group's last tile goes on
         fence_acq_rel();
-        is_last = (atomicAdd(&S.gdone[g], 1u) == (unsigned)(gt1 - gt0 - 1));
-    }
-    __syncthreads();
-    if (!is_last || threadIdx.x >= 32) return;  // warp 0 of the group's last tile goes on
-    fence_acq_rel();
-    int wall_g;
-    r = warp_reduce_partials(S.partials, gt0, gt1, sample, &wall_g);
-    if constexpr (TAN) tr = warp_reduce_partials(S.tpartials, gt0, gt1, sample, &wall_g);
-    unsigned prev = 0;
-    if (threadIdx.x == 0) {
-        store_partial(S.gpartials + g, r, wall_g);
-        if constexpr (TAN) store_partial(S.tgpartials + g, tr, wall_g);
-        S.gdone[g] = 0;
+        int wall_g;
+        r = warp_reduce_partials(S.partials, gt0, gt1, sample, &wall_g);
+        tr = warp_reduce_partials(S.tpartials, gt0, gt1, sample, &wall_g);
+        unsigned prev = 0;
+        if (threadIdx.x == 0) {
+            store_partial(S.gpartials + g, r, wall_g);
+            store_partial(S.tgpartials + g, tr, wall_g);
+            S.gdone[g] = 0;
+            fence_acq_rel();
+            prev = atomicAdd(&S.body[tank].done, 1u);
+        }
+        const unsigned n_groups = (unsigned)(S.group_first[tank + 1] - S.group_first[tank]);
+        if (__shfl_sync(0xffffffffu, prev, 0) != n_groups - 1) return;
         fence_acq_rel();
-        prev = atomicAdd(&S.body[tank].done, 1u);
+        int wall_t;
+        const Red rt = warp_reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall_t);
+        const Red trt = warp_reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall_t);
+        finish(rt, trt);
     }
-    const unsigned n_groups = (unsigned)(S.group_first[tank + 1] - S.group_first[tank]);
-    if (__shfl_sync(0xffffffffu, prev, 0) != n_groups - 1) return;
-    fence_acq_rel();
-    const double pre = finalize_preload(S, tank);
-    int wall_t;
-    const Red rt = warp_reduce_partials(S.gpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall_t);
-    Red trt = rt;
-    if constexpr (TAN) trt = warp_reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall_t);
-    tank_finalize(S, T, tank, eval, E, nbuf, sample, TAN, rt, trt, pre);
 }
 
 // ---------------------------------------------------------------------------
@@ -794,8 +893,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
 
 // Bins flat particles [N, 4] (tanks concatenated) into grid buffer `buf`,
 // anchored at each tank's stored anchor for that buffer.
-__global__ void bin_flat_kernel(SimDev S, const float4* __restrict__ xv, const int* __restrict__ part_tank, int n,
-                                int buf)
+__global__ void bin_flat_kernel(SimDev S, const float4* __restrict__ xv, const float4* __restrict__ lo,
+                                const int* __restrict__ part_tank, int n, int buf)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -812,6 +911,7 @@ __global__ void bin_flat_kernel(SimDev S, const float4* __restrict__ xv, const i
     const int slot = atomicAdd(&S.count[buf][cell], 1);
     if (slot < kCap) {
         S.pv[buf][cell * kCap + slot] = p;
+        S.lo[buf][cell * kCap + slot] = lo ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         S.pid[buf][cell * kCap + slot] = i;
     } else {
         flags |= SPH_FLAG_CELL_FULL;
@@ -838,6 +938,7 @@ __global__ void set_body_kernel(SimDev S, const double* __restrict__ body, int b
     b.anchor[buf][1] = s[1];
     b.tau_c = 0.0;
     b.done = 0;
+    for (int q = 0; q < 5; ++q) b.acc[q] = 0ull;
     b.dc = df_split(b.c);
     b.ds = df_split(b.s);
     b.drx = df_split(b.r[0]);
@@ -867,8 +968,10 @@ __global__ void get_body_kernel(SimDev S, double* __restrict__ body)
     o[5] = b.w;
 }
 
-// One warp per cell: scatter the occupied slots of buffer `buf` to [N, 4].
-__global__ void gather_state_kernel(SimDev S, float4* __restrict__ xv, int n_cells_total, int buf)
+// One warp per cell: scatter the occupied slots of buffer `buf` to [N, 4]
+// (the hi parts of the state; its lo parts to lo when given).
+__global__ void gather_state_kernel(SimDev S, float4* __restrict__ xv, float4* __restrict__ lo, int n_cells_total,
+                                    int buf)
 {
     const int cell = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -876,7 +979,9 @@ __global__ void gather_state_kernel(SimDev S, float4* __restrict__ xv, int n_cel
     const int n = min(S.count[buf][cell], kCap);
     if (lane < n) {
         const int gs = cell * kCap + lane;
-        xv[S.pid[buf][gs]] = S.pv[buf][gs];
+        const int id = S.pid[buf][gs];
+        if (xv) xv[id] = S.pv[buf][gs];
+        if (lo) lo[id] = S.lo[buf][gs];
     }
 }
 
@@ -1027,9 +1132,11 @@ cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_co
     return cudaSuccess;
 }
 
-cudaError_t launch_bin_flat(const SimDev& S, const float* xv, const int* part_tank, int n, int buf, cudaStream_t st)
+cudaError_t launch_bin_flat(const SimDev& S, const float* xv, const float* lo, const int* part_tank, int n, int buf,
+                            cudaStream_t st)
 {
-    if (n > 0) bin_flat_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, (const float4*)xv, part_tank, n, buf);
+    if (n > 0)
+        bin_flat_kernel<<<(n + 255) / 256, 256, 0, st>>>(S, (const float4*)xv, (const float4*)lo, part_tank, n, buf);
     return cudaGetLastError();
 }
 
@@ -1039,9 +1146,11 @@ cudaError_t launch_set_body(const SimDev& S, const double* body, int buf, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_get_state(const SimDev& S, float* xv, double* body, int n_cells_total, int buf, cudaStream_t st)
+cudaError_t launch_get_state(const SimDev& S, float* xv, float* lo, double* body, int n_cells_total, int buf,
+                             cudaStream_t st)
 {
-    if (xv && n_cells_total > 0) gather_state_kernel<<<(n_cells_total + 7) / 8, 256, 0, st>>>(S, (float4*)xv, n_cells_total, buf);
+    if ((xv || lo) && n_cells_total > 0)
+        gather_state_kernel<<<(n_cells_total + 7) / 8, 256, 0, st>>>(S, (float4*)xv, (float4*)lo, n_cells_total, buf);
     if (body) get_body_kernel<<<(S.B + 127) / 128, 128, 0, st>>>(S, body);
     return cudaGetLastError();
 }

@@ -17,9 +17,13 @@ cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_c
                          cudaStream_t st, bool pdl, bool tan = false);
 cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, cudaStream_t st,
                         bool pdl, bool tan = false);
-cudaError_t launch_bin_flat(const SimDev& S, const float* xv, const int* part_tank, int n, int buf, cudaStream_t st);
+// State transfer: xv [N, 4] the hi parts of the particle state, lo [N, 4] its
+// low parts (NULL: zero on binning, not read back on gathering).
+cudaError_t launch_bin_flat(const SimDev& S, const float* xv, const float* lo, const int* part_tank, int n, int buf,
+                            cudaStream_t st);
 cudaError_t launch_set_body(const SimDev& S, const double* body, int buf, cudaStream_t st);
-cudaError_t launch_get_state(const SimDev& S, float* xv, double* body, int n_cells_total, int buf, cudaStream_t st);
+cudaError_t launch_get_state(const SimDev& S, float* xv, float* lo, double* body, int n_cells_total, int buf,
+                             cudaStream_t st);
 // Tangent state: with txv_out == NULL sets the tangent from txv_in / tb_in
 // (NULL: zero); otherwise reads it into txv_out / tb_out.
 cudaError_t launch_tangent_state(const SimDev& S, const float* txv_in, float* txv_out, const double* tb_in,

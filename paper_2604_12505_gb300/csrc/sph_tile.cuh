@@ -44,6 +44,7 @@ struct Stage {
     int start[Sh::NC + 1];
     int own_row[TY + 1];
     float4 pv[Sh::MAXS];
+    float2 plo[Sh::MAXS];         // low parts (x_lo, y_lo) of the staged positions
     int pid[Sh::MAXS];
     int pid_in[Sh::MAXS];         // particle index in global slot order (before ordering)
     unsigned int key_in[Sh::MAXS];  // ordering key of x in global slot order
@@ -145,6 +146,8 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
         const int ix = cx0 - 1 + c % Sh::SX, iy = cy0 - 1 + c / Sh::SX;
         const int gs = (T.cell_base + iy * T.G + ix) * kCap + (e - a);
         sm.pv[d] = S.pv[buf][gs];
+        const float4 lo = S.lo[buf][gs];
+        sm.plo[d] = make_float2(lo.x, lo.y);
         if (RHO) sm.rho[d] = S.rhoP[gs];
         if constexpr (TAN) {
             sm.tpv[d] = S.tpv[buf][gs];
@@ -236,6 +239,8 @@ __device__ __forceinline__ bool stage_from_record(const SimDev& S, int tank, int
         if (i < total) {
             const int gs = r_slot[q];
             sm.pv[i] = S.pv[buf][gs];
+            const float4 lo = S.lo[buf][gs];
+            sm.plo[i] = make_float2(lo.x, lo.y);
             sm.rho[i] = S.rhoP[gs];
             if constexpr (TAN) {
                 sm.tpv[i] = S.tpv[buf][gs];

@@ -153,7 +153,7 @@ def identification_inputs(B: int, K: int, Ts: float, seed0: int) -> np.ndarray:
 
 def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, relax: int = 5000,
                     dt: float = 2e-4, cl_tanks: int = 64, cl_steps: int = 5000, n_sims: int = 65_536,
-                    fit_cfg: dict | None = None, seq_tanks: int = 8, seq_steps: int = 1000, ctrl=None,
+                    fit_cfg: dict | None = None, seq_tanks: int | None = None, seq_steps: int = 200, ctrl=None,
                     log=None, inputs: str = "piecewise") -> dict:
     """The surrogate workflow on the simulator and the LPV library.
 
@@ -161,7 +161,8 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
        once, ``launches`` open-loop runs of ``steps`` steps each with seeded
        inputs -- piecewise-constant holds (``inputs="piecewise"``) or the
        identification train scaled to the horizon (``inputs="train"``); the
-       batch step rate against the same tanks stepped one at a time.
+       batch step rate against the same tanks stepped one at a time (every
+       tank, ``seq_steps`` steps each, unless ``seq_tanks`` limits them).
     2. Fit (lpv.fit) on the trajectories of the first 80 % of the tanks, for
        the LPV model (p = [fill, thetadot]) and the LTI model (no scheduling).
     3. cl_tanks unseen tanks under unseen manoeuvres in closed loop with the PD
@@ -192,14 +193,19 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
     out["inputs"] = inputs
     d = dataset(tanks, u_l)
     npart = np.array(tanks.n_fluid, dtype=np.float64)
-    seq = sequential_rate(tanks, list(range(min(seq_tanks, n_tanks))), seq_steps)
+    n_seq = n_tanks if seq_tanks is None else min(seq_tanks, n_tanks)
+    seq = sequential_rate(tanks, list(range(n_seq)), seq_steps)
     s_batch = d["seconds"] / d["steps"]
-    s_seq = float(np.sum(seq) / npart[:len(seq)].sum() * npart.sum())
+    if n_seq == n_tanks:   # every tank timed alone: the sequential step is their sum
+        s_seq = float(np.sum(seq))
+        how = f"all {n_tanks} tanks alone, {seq_steps} steps each, summed"
+    else:
+        s_seq = float(np.sum(seq) / npart[:len(seq)].sum() * npart.sum())
+        how = f"{len(seq)} of {n_tanks} tanks alone, {seq_steps} steps each, scaled to all tanks by particle count"
     out["dataset"] = dict(trajectories=int(d["u"].shape[0]), samples=K, tanks=n_tanks, particles=int(npart.sum()),
                           device_s=d["seconds"], batched_ms_per_step=1e3 * s_batch,
                           sequential_ms_per_step=1e3 * s_seq, batched_speedup=s_seq / s_batch,
-                          sequential_sample=f"{len(seq)} of {n_tanks} tanks alone, {seq_steps} steps each, "
-                                            "scaled to all tanks by particle count")
+                          sequential_sample=how)
     say("dataset", out["dataset"])
     tanks.close()
 

@@ -51,3 +51,13 @@ def traj_err(yg, yr):
         d = np.linalg.norm(yg[:, cols] - yr[:, cols], axis=1).max()
         out[name] = d / np.linalg.norm(yr[:, cols], axis=1).max()
     return out
+
+
+def body_force_tolerance(ev, e_rho, rel=1e-5):
+    """Bound on |F_gpu - F_ref| per component (F_x, F_y, T_b) from the
+    arithmetic: the fluid-ghost pair forces that make up the body force carry
+    the error of their particle's density (e_rho, the measured maximum
+    relative density error) through Eq. 11, which the oracle's fb_drho sums as
+    rho df/drho over the pairs, plus FP32 rounding of each pair term, at most
+    ``rel`` of its magnitude (fb_abs)."""
+    return e_rho * np.asarray(ev["fb_drho"]) + rel * np.asarray(ev["fb_abs"]) + 1e-12

@@ -48,7 +48,9 @@ def _inner_pairs(sim, xv, body, u, K, v, w):
     return lhs_terms, rhs_terms, (xb0, bb0, ub)
 
 
-@pytest.mark.parametrize("cfg,K", [(dict(W.SMALL, outer_every=5), 30), (dict(W.JVP, outer_every=10), 20)])
+@pytest.mark.parametrize("cfg,K", [(dict(W.SMALL, outer_every=5), 30), (dict(W.JVP, outer_every=10), 20),
+                                   (dict(W.SMALL, outer_every=5, n_rings=1, ghost_spacing=0.9, gamma1=0.5,
+                                         ghost_pressure_clamp=1), 30)])
 def test_adjoint_is_the_transpose_of_the_tangent_map(orc, cfg, K):
     need_gpu()
     from paper_2604_12505_gb300.sph import Sim
