@@ -45,7 +45,8 @@ enum {
 /* Health flags raised on the device and reported by sph_check(). */
 enum {
     SPH_FLAG_NAN = 1,          /* a particle position or velocity became non-finite  */
-    SPH_FLAG_ESCAPED = 2,      /* a particle left the neighbour grid around the tank  */
+    SPH_FLAG_ESCAPED = 2,      /* a particle left the tank: beyond the ghost rings by  */
+                               /* more than a ring spacing and a grid cell            */
     SPH_FLAG_CELL_FULL = 4,    /* a grid cell exceeded SPH_CELL_CAPACITY particles    */
     SPH_FLAG_STAGE_FULL = 8,   /* a tile's staged neighbourhood exceeded shared memory */
     SPH_FLAG_TIMEOUT = 16      /* a bounded wait inside a persistent kernel gave up  */

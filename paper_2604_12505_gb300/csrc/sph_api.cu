@@ -107,6 +107,13 @@ void build_tank(TankHost& t)
     t.G = (int)std::ceil(2.0 * t.W / t.cell);
 }
 
+// Radius around the tank centre that the launched tiles cover: the outer
+// ghost ring plus a ring spacing and a grid cell.
+double cover_radius(const TankHost& t)
+{
+    return t.p.R + ((double)t.p.n_rings + 1.0) * ghost_ds(t.p) + t.cell;
+}
+
 template <class T>
 int dalloc(T** p, size_t n)
 {
@@ -270,6 +277,8 @@ TankDev make_tank_dev(const TankHost& t)
     for (int g = 0; g < t.n_g; ++g) rmin = std::min(rmin, std::hypot(t.gB[2 * g], t.gB[2 * g + 1]));
     const double rin = rmin - t.cell * 1.01;
     d.ghost_rin2 = rin > 0 ? (float)(rin * rin) : -1.0f;
+    d.Wf = (float)t.W;
+    d.cover2 = (float)(cover_radius(t) * cover_radius(t));
     d.clip = (float)(2.0 * t.h * (1.0 + 1e-3));
     d.hclip = (float)(t.h * (1.0 + 1e-3));
     d.g_cell = (float)t.cell;
@@ -374,12 +383,15 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
             const int G = th.G;
             // Launch order: tiles that meet the wall band first (their ghost
             // terms make them the longest, so they should take the first
-            // SM slots), then the interior, then the tiles outside the ghost
-            // rings (empty unless fluid has escaped); row-major within each.
+            // SM slots), then the interior; row-major within each.  Tiles
+            // wholly beyond the cover radius (the ghost rings plus a cell)
+            // are not launched: a particle there has escaped the tank and is
+            // flagged (SPH_FLAG_ESCAPED).  Every particle within the cover
+            // radius lies in a launched tile.
             const double inner = th.p.R - 3.0 * th.cell;
-            const double outer = th.p.R + ((double)th.p.n_rings + 1.0) * ghost_ds(th.p) + th.cell;
+            const double outer = cover_radius(th);
             int local = 0;
-            for (int cls = 0; cls < 3; ++cls)
+            for (int cls = 0; cls < 2; ++cls)
                 for (int ty = 0; ty < G; ty += TY)
                     for (int tx = 0; tx < G; tx += TX) {
                         // nearest and farthest distance of the tile from the tank centre
@@ -541,7 +553,11 @@ int get_state_full(sph_sim* sim, float* xv, float* lo, double* body, cudaStream_
 int set_state_full(sph_sim* sim, const float* xv, const float* lo, const double* body, cudaStream_t st)
 {
     const int buf = (int)(sim->host_step & 1);
+    // both buffers: the cells beyond the cover radius belong to no launched
+    // tile, so no density pass clears them, and a tile next to them stages
+    // them as halo
     CK(cudaMemsetAsync(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int), st));
+    CK(cudaMemsetAsync(sim->S.count[buf ^ 1], 0, sim->n_cells_total * sizeof(int), st));
     CK(launch_set_body(sim->S, body, buf, st));
     CK(launch_bin_flat(sim->S, xv, lo, sim->d_part_tank, sim->n_f_total, buf, st));
     return SPH_OK;
@@ -952,6 +968,7 @@ int sph_autotune(sph_sim* sim, int32_t steps, int32_t* chosen, double* us_per_st
         CK(cudaMemcpy(sim->d_run, &run, sizeof(RunDev), cudaMemcpyHostToDevice));
         const int buf = (int)(step0 & 1);
         CK(cudaMemset(sim->S.count[buf], 0, sim->n_cells_total * sizeof(int)));
+        CK(cudaMemset(sim->S.count[buf ^ 1], 0, sim->n_cells_total * sizeof(int)));
         CK(launch_bin_flat(sim->S, sim->d_scratch_xv, sim->d_scratch_lo, sim->d_part_tank, sim->n_f_total, buf, st));
         CK(cudaStreamSynchronize(st));
     }

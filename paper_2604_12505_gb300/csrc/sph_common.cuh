@@ -46,6 +46,8 @@ struct TankDev {
     float hclip;                  // h (1 + 1e-3): likewise for the ghost terms of the force pass (support h)
     float g_cell;                 // fl32(ghost-grid cell side)
     int gp_clamp;                 // Eq. 16 with max(P_i, 0)
+    float Wf;                     // fl32(grid half-width W)
+    float cover2;                 // fl32(cover radius^2): beyond it no tile is launched
     int G;                        // cells per side (fluid and ghost grid)
     int n_f, n_g;
     int cell_base;                // first cell of this tank in the global grid arrays

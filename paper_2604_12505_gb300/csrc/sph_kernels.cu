@@ -756,10 +756,11 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 bool out = false;
                 const int ccx = cell_coord(x, ox, T.inv_cell, T.G, &out);
                 const int ccy = cell_coord(y, oy, T.inv_cell, T.G, &out);
-                if (out) flags |= SPH_FLAG_ESCAPED;
+                const float ex = x - (ox + T.Wf), ey = y - (oy + T.Wf);   // from the next grid's centre
+                if (out || fmaf(ex, ex, ey * ey) > T.cover2) flags |= SPH_FLAG_ESCAPED;
                 const int cell = T.cell_base + ccy * T.G + ccx;
                 const int slot = atomicAdd(&S.count[nbuf][cell], 1);
-                if (slot < kCap) {
+                if ((unsigned)slot < (unsigned)kCap) {
                     S.pv[nbuf][cell * kCap + slot] = make_float4(x, y, vx, vy);
                     S.lo[nbuf][cell * kCap + slot] = make_float4(dx2.y, dy2.y, kx.y, ky.y);
                     S.pid[nbuf][cell * kCap + slot] = id;
@@ -905,11 +906,12 @@ __global__ void bin_flat_kernel(SimDev S, const float4* __restrict__ xv, const f
     const float ox = (float)(b.anchor[buf][0] - T.W), oy = (float)(b.anchor[buf][1] - T.W);
     bool out = false;
     const int cx = cell_coord(p.x, ox, T.inv_cell, T.G, &out), cy = cell_coord(p.y, oy, T.inv_cell, T.G, &out);
-    int flags = out ? SPH_FLAG_ESCAPED : 0;
+    const float ex = p.x - (ox + T.Wf), ey = p.y - (oy + T.Wf);
+    int flags = (out || fmaf(ex, ex, ey * ey) > T.cover2) ? SPH_FLAG_ESCAPED : 0;
     if (!(isfinite(p.x) && isfinite(p.y) && isfinite(p.z) && isfinite(p.w))) flags |= SPH_FLAG_NAN;
     const int cell = T.cell_base + cy * T.G + cx;
     const int slot = atomicAdd(&S.count[buf][cell], 1);
-    if (slot < kCap) {
+    if ((unsigned)slot < (unsigned)kCap) {
         S.pv[buf][cell * kCap + slot] = p;
         S.lo[buf][cell * kCap + slot] = lo ? lo[i] : make_float4(0.f, 0.f, 0.f, 0.f);
         S.pid[buf][cell * kCap + slot] = i;

@@ -78,7 +78,7 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
     for (int c = tid; c < Sh::NC; c += blockDim.x) {
         int ix = cx0 - 1 + c % Sh::SX, iy = cy0 - 1 + c / Sh::SX;
         int n = 0;
-        if (ix >= 0 && ix < T.G && iy >= 0 && iy < T.G) n = min(count[T.cell_base + iy * T.G + ix], kCap);
+        if (ix >= 0 && ix < T.G && iy >= 0 && iy < T.G) n = min(max(count[T.cell_base + iy * T.G + ix], 0), kCap);
         sm.start[c] = n;
     }
     __syncthreads();

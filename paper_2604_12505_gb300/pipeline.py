@@ -327,7 +327,7 @@ def linearization_study(cfg: dict | None = None, relax: int = 2000, steps: int =
 
 
 def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int = 64, jitter: float = 0.25,
-                         seed: int = 0, gammas=None, log=None) -> dict:
+                         seed: int = 0, gammas=None, extra: dict | None = None, log=None) -> dict:
     """The paper's benchmark spacecraft (Section 5.1, Tables 1 and 2) on this
     GPU, as context for the simulation times the paper reports (Table 3).
 
@@ -344,12 +344,14 @@ def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int 
     checked every second, against the outermost ghost ring) and on `batch`
     copies with their own spawns and inputs stepped together.  The health flags (SPH_FLAG_*)
     after the relaxation and after each flight are recorded; a gamma1 whose
-    relaxation already lets fluid through the wall is not flown."""
+    relaxation already lets fluid through the wall is not flown.  `extra`
+    (e.g. dict(ghost_pressure_clamp=1), reading R34) is applied to Table 2's
+    walls."""
     from . import workloads as W
     from .sph import Sim, gamma1_estimate
 
     say = log or (lambda *a: None)
-    base = dict(W.PAPER)
+    base = dict(W.PAPER, **(extra or {}))
     outer, dt = base["outer_every"], base["dt"]
     Ts = outer * dt
     K = int(round(seconds / Ts))
@@ -380,7 +382,8 @@ def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int 
         return vmax, flags
 
     for cfg in walls:
-        run = dict(gamma1=cfg["gamma1"], rings=cfg["n_rings"], ghost_spacing=cfg["ghost_spacing"])
+        run = dict(gamma1=cfg["gamma1"], rings=cfg["n_rings"], ghost_spacing=cfg["ghost_spacing"],
+                   ghost_pressure_clamp=cfg.get("ghost_pressure_clamp", 0))
         with Sim(cfg) as sim:
             run["particles"], run["ghosts"] = sim.n_fluid[0], sim.n_ghost[0]
             run["relax_vmax"], run["relax_flags"] = spawn(sim, [seed])
@@ -565,9 +568,11 @@ if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "linearize":
         print(json.dumps(linearization_study(log=lambda *a: print(*a, file=sys.stderr))))
     elif len(sys.argv) > 1 and sys.argv[1] == "paper":
-        print(json.dumps(paper_scenario_study(log=lambda *a: print(*a, file=sys.stderr))))
+        # "paper clamp": Table 2's walls with reading R34 (Eq. 16 with max(P_i, 0))
+        extra = dict(ghost_pressure_clamp=1) if "clamp" in sys.argv[2:] else None
+        print(json.dumps(paper_scenario_study(extra=extra, log=lambda *a: print(*a, file=sys.stderr))))
     elif len(sys.argv) > 1 and sys.argv[1] == "velocity":
         print(json.dumps(velocity_surrogate_study(log=lambda *a: print(*a, file=sys.stderr))))
     else:
-        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper|velocity", file=sys.stderr)
+        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper [clamp]|velocity", file=sys.stderr)
         sys.exit(2)
