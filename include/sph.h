@@ -298,10 +298,10 @@ int sph_set_tile(sph_sim* sim, int32_t tile);
 int sph_autotune(sph_sim* sim, int32_t steps, int32_t* chosen, double* us_per_step, void* stream);
 
 /*
- * Advances n_steps with zero input, launching the two kernels of a step
- * (density pass, force pass) one by one with CUDA events between them on
- * `stream`; host us[2] receives their mean durations in microseconds.
- * Blocks.
+ * Advances n_steps with zero input, launching the three kernels of a step
+ * (density pass, force pass, body update) one by one with CUDA events
+ * between them on `stream`; host us[3] receives their mean durations in
+ * microseconds.  Blocks.
  */
 int sph_time_kernels(sph_sim* sim, int32_t n_steps, double* us, void* stream);
 

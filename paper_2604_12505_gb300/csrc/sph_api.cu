@@ -989,26 +989,26 @@ int sph_time_kernels(sph_sim* sim, int32_t n_steps, double* us, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     RunDev d{};
     CK(launch_set_run(sim->d_run, d, st));
-    cudaEvent_t ev[3];
+    cudaEvent_t ev[4];
     for (auto& e : ev) CK(cudaEventCreate(&e));
-    double acc[2] = {0.0, 0.0};
+    double acc[3] = {0.0, 0.0, 0.0};
     const SimDev S = sim->dev();
     EvalOut E{};
     for (int i = 0; i < n_steps; ++i) {
-        for (int ph = 0; ph < 2; ++ph) {
+        for (int ph = 0; ph < 3; ++ph) {
             CK(cudaEventRecord(ev[ph], st));
             CK(launch_phase(S, E, 0, sim->tile_code, sim->n_tiles[sim->tile_code], ph, st, false));
         }
-        CK(cudaEventRecord(ev[2], st));
-        CK(cudaEventSynchronize(ev[2]));
-        for (int ph = 0; ph < 2; ++ph) {
+        CK(cudaEventRecord(ev[3], st));
+        CK(cudaEventSynchronize(ev[3]));
+        for (int ph = 0; ph < 3; ++ph) {
             float ms = 0.f;
             CK(cudaEventElapsedTime(&ms, ev[ph], ev[ph + 1]));
             acc[ph] += ms;
         }
     }
     for (auto& e : ev) cudaEventDestroy(e);
-    for (int ph = 0; ph < 2; ++ph) us[ph] = 1000.0 * acc[ph] / n_steps;
+    for (int ph = 0; ph < 3; ++ph) us[ph] = 1000.0 * acc[ph] / n_steps;
     sim->host_step += n_steps;
     return SPH_OK;
 }

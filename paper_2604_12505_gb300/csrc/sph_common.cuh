@@ -22,6 +22,7 @@
 //     every ghost it visits and read by the force pass.
 //   * per tank: FP32/FP64 constants (TankDev), FP64 body state (BodyDev).
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -85,6 +86,12 @@ struct BodyDev {
     unsigned int done;            // tiles (reduction groups in the tangent variant) finished in the current force pass
     int flags;                    // SPH_FLAG_* bits
 };
+// the body update stores these fields by lane (consecutive fields of one type)
+static_assert(offsetof(BodyDev, th) == 2 * sizeof(double) && offsetof(BodyDev, s) == 7 * sizeof(double),
+              "r, theta, rdot, thetadot, cos, sin lead BodyDev");
+static_assert(offsetof(BodyDev, fo_next) == offsetof(BodyDev, fc) + 4 * sizeof(float), "fc .. fo_next contiguous");
+static_assert(offsetof(BodyDev, dry) == offsetof(BodyDev, dc) + 3 * sizeof(float2), "dc .. dry contiguous");
+static_assert(offsetof(BodyDev, fw) == offsetof(BodyDev, fvx) + 2 * sizeof(float), "fvx .. fw contiguous");
 
 // Fixed point of the body accumulators: a value v is held as round(v 2^32).
 // A two-float (hi, lo) sum converts term by term; scaling by a power of two

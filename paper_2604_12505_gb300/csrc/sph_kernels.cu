@@ -42,7 +42,6 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     using Sh = Shape<TX, TY>;
     __shared__ Stage<TX, TY, false, TAN> sm;
     __shared__ GhostStage<!TAN> gs;
-    pdl_trigger();
     const int4 td = S.tiles[blockIdx.x];
     const TankDev T = S.tank[td.x];  // by value: the constants live in registers
     const int cx0 = td.y, cy0 = td.z;
@@ -191,11 +190,20 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             if (E.nbr) E.nbr[3 * id + 1] = ng2;
         }
     }
+    // the successor's CTAs may be placed once every CTA of this pass is past
+    // its particle loop (or has exited): placed earlier, they would wait in
+    // griddepcontrol.wait on SM slots that tiles of this pass still need
+    pdl_trigger();
 }
 
 // ---------------------------------------------------------------------------
 // Block reductions (fixed order: deterministic)
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ F2 shfl_f2(F2 v)
+{
+    return F2{__shfl_sync(0xffffffffu, v.hi, 0), __shfl_sync(0xffffffffu, v.lo, 0)};
+}
+
 __device__ __forceinline__ F2 shfl_down_f2(F2 v, int o)
 {
     return F2{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
@@ -208,10 +216,10 @@ struct Red {
 
 // Sums over a warp (result valid in lane 0).  Only the parts flagged by the
 // uniform switches are reduced.
-__device__ __forceinline__ Red warp_reduce(Red r, bool forces, bool com)
+__device__ __forceinline__ Red warp_reduce(Red r, bool forces, bool com, int first = 16)
 {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
+    for (int o = first; o > 0; o >>= 1) {
         if (forces) {
             r.fx = f2_add(r.fx, shfl_down_f2(r.fx, o));
             r.fy = f2_add(r.fy, shfl_down_f2(r.fy, o));
@@ -226,7 +234,9 @@ __device__ __forceinline__ Red warp_reduce(Red r, bool forces, bool com)
     return r;
 }
 
-// Sums over the block (result valid in thread 0).
+// Sums over the block (result valid in thread 0): each warp's sum, then the
+// warps' sums by a fixed shuffle tree in warp 0 (blockDim a power-of-two
+// multiple of 32).
 __device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* one per warp */)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -234,19 +244,10 @@ __device__ Red block_reduce(Red r, bool forces, bool com, Red* scratch /* one pe
     __syncthreads();
     if (lane == 0) scratch[warp] = r;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < nw; ++w) {
-            if (forces) {
-                r.fx = f2_add(r.fx, scratch[w].fx);
-                r.fy = f2_add(r.fy, scratch[w].fy);
-                r.t = f2_add(r.t, scratch[w].t);
-            }
-            if (com) {
-                r.cx = f2_add(r.cx, scratch[w].cx);
-                r.cy = f2_add(r.cy, scratch[w].cy);
-            }
-            r.pairs += scratch[w].pairs;
-        }
+    if (warp == 0 && nw > 1) {
+        const F2 z{0.f, 0.f};
+        r = lane < nw ? scratch[lane] : Red{z, z, z, z, z, 0ull};
+        r = warp_reduce(r, forces, com, nw >> 1);
     }
     return r;
 }
@@ -321,7 +322,8 @@ __device__ Red warp_reduce_partials(const TilePartial* P, int p0, int p1, bool c
 // leading doubles of BodyDev), the held control torque (8), the input of this
 // step (9..11), the controller's J, omega, xi (12..14), the reference angle of
 // this sample (15), the controller / held-tank switches (16), the sample
-// output pointer (17), the call's first step (18) and the sample stride (19).
+// output pointer (17), the call's first step (18), the sample stride (19) and
+// the step (20).
 __device__ __forceinline__ double finalize_preload(const SimDev& S, const TankDev& T, int tank)
 {
     const int lane = (int)(threadIdx.x & 31);
@@ -355,14 +357,50 @@ __device__ __forceinline__ double finalize_preload(const SimDev& S, const TankDe
         pre = __longlong_as_double(step0);
     } else if (lane == 19) {
         pre = __longlong_as_double(run->y_tank_stride);
+    } else if (lane == 20) {
+        pre = __longlong_as_double(step);
     }
     return pre;
+}
+
+// cos and sin of theta + dtheta from those of theta: for |dtheta| <= 1e-2 the
+// angle-addition formulas with Taylor series of cos and sin of dtheta (their
+// first omitted terms are below 1e-16 relative) and one Newton step that
+// keeps cos^2 + sin^2 at 1; otherwise FP64 sincos of the new angle.  The
+// dependent FP64 chain is a quarter of sincos's, and it is on the serial
+// path of every step.
+__device__ __forceinline__ void rotate(double dth, double th_new, double& c, double& s)
+{
+    if (fabs(dth) > 1e-2) {
+        sincos(th_new, &s, &c);
+        return;
+    }
+    const double d2 = dth * dth;
+    const double cd = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0 - d2 * (1.0 / 720.0)));
+    const double sd = dth * (1.0 - d2 * (1.0 / 6.0 - d2 * (1.0 / 120.0 - d2 * (1.0 / 5040.0))));
+    const double c1 = c * cd - s * sd, s1 = s * cd + c * sd;
+    const double f = 1.5 - 0.5 * (c1 * c1 + s1 * s1);
+    c = c1 * f;
+    s = s1 * f;
+}
+
+// The value at position `lane` of the list (0 past its end): nested selects,
+// so the lanes of a warp pick different values without diverging.
+__device__ __forceinline__ double pick(int, int) { return 0.0; }
+template <class... R>
+__device__ __forceinline__ double pick(int lane, int i, double x, R... rest)
+{
+    return lane == i ? x : pick(lane, i + 1, rest...);
 }
 
 // Fx, Fy, Tq: fluid force and torque on the body (Eq. 20); Cx, Cy: sums of the
 // particle positions (sample steps only).  add_pairs: pair interactions of the
 // pass still to be added to the tank's count (the tiles of the step pass add
 // theirs themselves).  tr: tangent of the reduced sums (TAN only).
+// Every lane of warp 0 computes the same FP64 body update (one warp
+// instruction costs the same for one lane as for all), and the lanes then
+// convert and store one field each, so the stores of the body record, its
+// FP32 forms and the sample are one short parallel step.
 __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int eval, const EvalOut& E, int nbuf,
                               long long step, bool sample, bool tan, double Fx, double Fy, double Tq, double Cx,
                               double Cy, unsigned long long add_pairs, const Red& tr, double pre)
@@ -383,35 +421,30 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
     double* const yout = (double*)__double_as_longlong(__shfl_sync(0xffffffffu, pre, 17));
     const long long step0 = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 18));
     const long long ystride = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 19));
-    if (lane != 0) return;
     const long long k = step - step0;
     const bool ctrl_on = (sw & 1) != 0, body_fixed = (sw & 2) != 0;
 
-    // FP64 from here on: assembly of the body state
+    // FP64 from here on: assembly of the body state.  The serial chain runs
+    // in lane 0 alone: on this GPU's narrow FP64 pipe a warp instruction costs
+    // in proportion to its active lanes.
     if (sample) {
         const long long oe = T.outer_every;
         const long long row = step / oe - (step0 + oe - 1) / oe;
         if (ctrl_on) {  // Eq. 28 under zero-order hold
-            const double Jc = cJ > 0.0 ? cJ : T.J_body;
-            tau_c = Jc * cw * cw * (ref - th) - 2.0 * cxi * Jc * cw * w;
-            bp->tau_c = tau_c;
+            if (lane == 0) {
+                const double Jc = cJ > 0.0 ? cJ : T.J_body;
+                tau_c = Jc * cw * cw * (ref - th) - 2.0 * cxi * Jc * cw * w;
+                bp->tau_c = tau_c;
+            }
         }
-        if (yout) {
-            double* y = yout + tank * ystride + row * SPH_NY;
-            y[0] = rx;
-            y[1] = ry;
-            y[2] = th;
-            y[3] = vx;
-            y[4] = vy;
-            y[5] = w;
-            y[6] = Fx;
-            y[7] = Fy;
-            y[8] = Tq;
-            y[9] = T.n_f ? Cx / T.n_f : 0.0;
-            y[10] = T.n_f ? Cy / T.n_f : 0.0;
+        if (yout && lane < SPH_NY) {
+            double v = pick(lane, 0, rx, ry, th, vx, vy, w, Fx, Fy, Tq);
+            if (lane == 9) v = T.n_f ? Cx / T.n_f : 0.0;
+            if (lane == 10) v = T.n_f ? Cy / T.n_f : 0.0;
+            yout[tank * ystride + row * SPH_NY + lane] = v;
         }
     }
-    if (tan && !eval) {  // tangent of Eq. 20 and of the kick-then-drift body step
+    if (tan && !eval && lane == 0) {  // tangent of Eq. 20 and of the kick-then-drift body step
         const double dFx = (double)tr.fx.hi + (double)tr.fx.lo;
         const double dFy = (double)tr.fy.hi + (double)tr.fy.lo;
         const double dTq = (double)tr.t.hi + (double)tr.t.lo;
@@ -454,7 +487,7 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
         b.ftv[1] = (float)b.tv[1];
         b.ftw = (float)b.tw;
     }
-    if (tan && eval && E.dbody) {  // tangent of the evaluation's body outputs (no controller)
+    if (tan && eval && E.dbody && lane == 0) {  // tangent of the evaluation's body outputs (no controller)
         const double dFx = (double)tr.fx.hi + (double)tr.fx.lo;
         const double dFy = (double)tr.fy.hi + (double)tr.fy.lo;
         const double dTq = (double)tr.t.hi + (double)tr.t.lo;
@@ -473,53 +506,53 @@ __device__ void tank_finalize(const SimDev& S, const TankDev& T, int tank, int e
         o[4] = (dFy + duy) * T.inv_m_body;
         o[5] = (dTq + dut) * T.inv_J_body;
     }
-    const double tau = ut + (ctrl_on ? tau_c : 0.0);
-    const double ax = (Fx + ux) * T.inv_m_body, ay = (Fy + uy) * T.inv_m_body, aw = (Tq + tau) * T.inv_J_body;
-    if (eval) {
-        if (E.body) {
-            double* o = E.body + 6 * tank;
-            o[0] = Fx;
-            o[1] = Fy;
-            o[2] = Tq;
-            o[3] = ax;
-            o[4] = ay;
-            o[5] = aw;
-        }
-    } else {
-        bp->anchor[nbuf][0] = rx;
-        bp->anchor[nbuf][1] = ry;
-        if (!body_fixed) {
+    double ax = 0.0, ay = 0.0, aw = 0.0;
+    if (lane == 0) {
+        const double tau = ut + (ctrl_on ? tau_c : 0.0);
+        ax = (Fx + ux) * T.inv_m_body;
+        ay = (Fy + uy) * T.inv_m_body;
+        aw = (Tq + tau) * T.inv_J_body;
+        if (!eval && !body_fixed) {
             vx += T.dt_d * ax;  // kick then drift (Section 3.4)
             vy += T.dt_d * ay;
             w += T.dt_d * aw;
             rx += T.dt_d * vx;
             ry += T.dt_d * vy;
-            th += T.dt_d * w;
-            sincos(th, &sn, &c);
-            bp->v[0] = vx;
-            bp->v[1] = vy;
-            bp->w = w;
-            bp->r[0] = rx;
-            bp->r[1] = ry;
-            bp->th = th;
-            bp->s = sn;
-            bp->c = c;
+            const double dth = T.dt_d * w;
+            th += dth;
+            rotate(dth, th, c, sn);
         }
-        bp->dc = df_split(c);
-        bp->ds = df_split(sn);
-        bp->drx = df_split(rx);
-        bp->dry = df_split(ry);
-        bp->fvx = (float)vx;
-        bp->fvy = (float)vy;
-        bp->fw = (float)w;
-        bp->fc = (float)c;
-        bp->fs = (float)sn;
-        bp->frx = (float)rx;
-        bp->fry = (float)ry;
-        bp->fo_next[0] = (float)(rx - T.W);
-        bp->fo_next[1] = (float)(ry - T.W);
-        bp->pairs += add_pairs;
     }
+    if (eval) {
+        ax = __shfl_sync(0xffffffffu, ax, 0);
+        ay = __shfl_sync(0xffffffffu, ay, 0);
+        aw = __shfl_sync(0xffffffffu, aw, 0);
+        if (E.body && lane < 6) E.body[6 * tank + lane] = pick(lane, 0, Fx, Fy, Tq, ax, ay, aw);
+    } else {
+        if (lane < 2) bp->anchor[nbuf][lane] = lane ? ry : rx;  // the state before the step (unchanged in lanes 1..)
+        rx = __shfl_sync(0xffffffffu, rx, 0);
+        ry = __shfl_sync(0xffffffffu, ry, 0);
+        th = __shfl_sync(0xffffffffu, th, 0);
+        vx = __shfl_sync(0xffffffffu, vx, 0);
+        vy = __shfl_sync(0xffffffffu, vy, 0);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        c = __shfl_sync(0xffffffffu, c, 0);
+        sn = __shfl_sync(0xffffffffu, sn, 0);
+        // the leading doubles of BodyDev: r, theta, rdot, thetadot, cos, sin
+        if (!body_fixed && lane < 8) reinterpret_cast<double*>(bp)[lane] = pick(lane, 0, rx, ry, th, vx, vy, w, c, sn);
+        // FP32 forms: two-float splits (lanes 0-3: dc, ds, drx, dry), rounded
+        // values (lanes 4-9: fc, fs, frx, fry, fo_next; lanes 10-12: fvx, fvy, fw)
+        if (lane < 13) {
+            double d = pick(lane, 0, c, sn, rx, ry, c, sn, rx, ry, rx, ry, vx, vy, w);
+            if (lane == 8 || lane == 9) d -= T.W;
+            const float hi = (float)d;
+            if (lane < 4) (&bp->dc)[lane] = make_float2(hi, (float)(d - (double)hi));
+            else if (lane < 10) (&bp->fc)[lane - 4] = hi;
+            else (&bp->fvx)[lane - 10] = hi;
+        }
+        if (lane == 0) bp->pairs += add_pairs;
+    }
+    if (lane != 0) return;
     bp->done = 0;
     if (S.B == 1) {  // the only tank: its step is the pass's (visible when the kernel completes)
         if (!eval) run->step = step + 1;
@@ -554,7 +587,6 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     __shared__ GhostStage<!TAN> gs;
     __shared__ Red scratch[32];
     __shared__ int is_last;
-    pdl_trigger();
     const int4 td = S.tiles[blockIdx.x];
     const int tank = td.x;
     const TankDev T = S.tank[tank];  // by value: the constants live in registers
@@ -563,19 +595,16 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     const long long step = S.run->step;
     const int buf = (int)(step & 1), nbuf = buf ^ 1;
     const bool sample = !eval && (step % T.outer_every) == 0;
-    // what the body update reads, in flight while the tile is staged (only
-    // the tank's last tile uses it)
-    double pre = 0.0;
-    if (threadIdx.x < 32) pre = finalize_preload(S, T, tank);
     const float damp = 1.0f - S.run->damping;
 
     const F2 z{0.f, 0.f};
     Red acc{z, z, z, z, z, 0ull};
     Red tacc{z, z, z, z, z, 0ull};
-    int flags = 0, wall = 0;
+    int flags = 0, wall = 0, own = 0;
     if (stage_from_record<TX, TY, TAN>(S, tank, buf, stage_record<TX, TY>(S, blockIdx.x), sm)) {
         const BodyDev& b = S.body[tank];
         const int n_own = sm.own_row[TY];
+        own = n_own;
         int gmode = kGhostsGlobal;  // the tangent variant visits the ghosts through global memory
         if constexpr (!TAN) gmode = n_own > 0 ? stage_ghosts<false>(S, T, b, sm, n_own, gs) : kGhostsNone;
         const float bc = b.fc, bs = b.fs, brx = b.frx, bry = b.fry;
@@ -590,7 +619,6 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             const float2 li = sm.plo[e];
             const float2 ri = sm.rho[e];
             const int c = sm.cell[e];
-            const float4 lo4 = eval ? make_float4(0.f, 0.f, 0.f, 0.f) : S.lo[buf][sm.slot[e]];  // for the integration
             float ax = 0.f, ay = 0.f, tax = 0.f, tay = 0.f;
             float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
             float2 tri = make_float2(0.f, 0.f);
@@ -743,14 +771,15 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             } else {
                 // kick then drift (Section 3.4) on the two-float state, then bin
                 // into the next grid: v' = (v + dt a)(1 - c), x' = x + dt v'
-                float2 kx = two_sum(pi.z, fmaf(T.dt, ax, lo4.z)), ky = two_sum(pi.w, fmaf(T.dt, ay, lo4.w));
+                const float2 vl = sm.vlo[e];
+                float2 kx = two_sum(pi.z, fmaf(T.dt, ax, vl.x)), ky = two_sum(pi.w, fmaf(T.dt, ay, vl.y));
                 if (damp != 1.0f) {  // relaxation: scale the two-float velocity
                     const float hx = kx.x * damp, hy = ky.x * damp;
                     kx = two_sum(hx, fmaf(kx.x, damp, -hx) + kx.y * damp);
                     ky = two_sum(hy, fmaf(ky.x, damp, -hy) + ky.y * damp);
                 }
-                const float2 dx2 = two_sum(pi.x, fmaf(T.dt, kx.x, fmaf(T.dt, kx.y, lo4.x)));
-                const float2 dy2 = two_sum(pi.y, fmaf(T.dt, ky.x, fmaf(T.dt, ky.y, lo4.y)));
+                const float2 dx2 = two_sum(pi.x, fmaf(T.dt, kx.x, fmaf(T.dt, kx.y, li.x)));
+                const float2 dy2 = two_sum(pi.y, fmaf(T.dt, ky.x, fmaf(T.dt, ky.y, li.y)));
                 const float vx = kx.x, vy = ky.x, x = dx2.x, y = dy2.x;
                 if (!(isfinite(x) && isfinite(y) && isfinite(vx) && isfinite(vy))) flags |= SPH_FLAG_NAN;
                 bool out = false;
@@ -785,47 +814,36 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         tacc.cx = F2{tcxs, 0.f};
         tacc.cy = F2{tcys, 0.f};
     }
+    pdl_trigger();  // past the particle loop (see the density pass)
     if (flags) atomicOr(&S.body[tank].flags, flags);
-    const bool any_wall = __syncthreads_or(wall) != 0;
-    Red r = block_reduce(acc, any_wall, sample, scratch);
-    const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
     if constexpr (!TAN) {
         // The tile's sums go into the tank's fixed-point accumulators by
         // integer atomics (order-independent, so every run, and a tank run
-        // alone or in a batch, gets the same bits); the tank's last tile, by
-        // a counter of finished tiles, reads them and updates the body.
+        // alone or in a batch, gets the same bits); the body kernel that
+        // follows this pass reads them.  A tile without own particles adds
+        // nothing.
+        if (own == 0) return;  // uniform over the block
         BodyDev* bp = S.body + tank;
-        if (threadIdx.x == 0) {
-            if (any_wall) {
-                fix_add(&bp->acc[0], r.fx);
-                fix_add(&bp->acc[1], r.fy);
-                fix_add(&bp->acc[2], r.t);
-            }
-            if (sample) {
-                fix_add(&bp->acc[3], r.cx);
-                fix_add(&bp->acc[4], r.cy);
-            }
-            if (!eval && r.pairs) atomicAdd(&bp->pairs, r.pairs);
-            fence_acq_rel();
-            is_last = (atomicAdd(&bp->done, 1u) == (unsigned)(t1 - t0 - 1));
-        }
-        __syncthreads();
-        if (!is_last || threadIdx.x >= 32) return;
-        fence_acq_rel();
-        const int lane = (int)threadIdx.x;
-        long long q = 0;
-        if (lane < 5) {
-            q = (long long)__ldcg(&bp->acc[lane]);
-            bp->acc[lane] = 0ull;  // cleared for the next pass (every addition of this one is counted)
-        }
-        const double Fx = (double)__shfl_sync(0xffffffffu, q, 0) * kFixUnit;
-        const double Fy = (double)__shfl_sync(0xffffffffu, q, 1) * kFixUnit;
-        const double Tq = (double)__shfl_sync(0xffffffffu, q, 2) * kFixUnit;
-        const double Cx = (double)__shfl_sync(0xffffffffu, q, 3) * kFixUnit;
-        const double Cy = (double)__shfl_sync(0xffffffffu, q, 4) * kFixUnit;
-        tank_finalize(S, T, tank, eval, E, nbuf, step, sample, false, Fx, Fy, Tq, Cx, Cy, 0ull, r, pre);
+        const int lane = (int)(threadIdx.x & 31);
+        const bool any_wall = __syncthreads_or(wall) != 0;
+        const Red r = block_reduce(acc, any_wall, sample, scratch);
+        if (threadIdx.x >= 32) return;
+        // lane q adds component q (F_x, F_y, T on wall tiles; the position
+        // sums on sample steps), lane 5 the pair count
+        const F2 fx = shfl_f2(r.fx), fy = shfl_f2(r.fy), tq = shfl_f2(r.t), cx = shfl_f2(r.cx), cy = shfl_f2(r.cy);
+        const unsigned long long pairs = __shfl_sync(0xffffffffu, r.pairs, 0);
+        const F2 mine = lane == 0 ? fx : lane == 1 ? fy : lane == 2 ? tq : lane == 3 ? cx : cy;
+        if ((lane < 3 && any_wall) || (lane >= 3 && lane < 5 && sample)) fix_add(&bp->acc[lane], mine);
+        if (lane == 5 && !eval && pairs) atomicAdd(&bp->pairs, pairs);
         return;
     } else {
+        // what the body update reads, in flight during the tile's reduction
+        // (only the tank's last tile uses it)
+        double pre = 0.0;
+        if (threadIdx.x < 32) pre = finalize_preload(S, T, tank);
+        const int t0 = S.tile_tank_first[tank], t1 = S.tile_tank_first[tank + 1];
+        const bool any_wall = __syncthreads_or(wall) != 0;
+        Red r = block_reduce(acc, any_wall, sample, scratch);
         // Tangent variant: fixed-order reduction of the tile partials (the
         // tangent's scale is the caller's, unsuited to a fixed point).  One
         // level when the tank's last tile can fetch them with at most
@@ -834,11 +852,12 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         // levels: the last tile of each group of kTileGroup tiles sums the
         // group, the last group of the tank sums the groups.
         Red tr = block_reduce(tacc, any_wall, sample, scratch);
+        // called by all of warp 0 with the sums valid in lane 0: every lane
+        // of the body update needs them
         auto finish = [&](const Red& rt, const Red& trt) {
-            tank_finalize(S, T, tank, eval, E, nbuf, step, sample, true, (double)rt.fx.hi + (double)rt.fx.lo,
-                          (double)rt.fy.hi + (double)rt.fy.lo, (double)rt.t.hi + (double)rt.t.lo,
-                          (double)rt.cx.hi + (double)rt.cx.lo, (double)rt.cy.hi + (double)rt.cy.lo, rt.pairs, trt,
-                          pre);
+            auto all = [](F2 v) { return __shfl_sync(0xffffffffu, (double)v.hi + (double)v.lo, 0); };
+            tank_finalize(S, T, tank, eval, E, nbuf, step, sample, true, all(rt.fx), all(rt.fy), all(rt.t),
+                          all(rt.cx), all(rt.cy), rt.pairs, trt, pre);
         };
         if (t1 - t0 <= kOneLevelLoads * (int)blockDim.x) {
             if (threadIdx.x == 0) {
@@ -886,6 +905,42 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         const Red trt = warp_reduce_partials(S.tgpartials, S.group_first[tank], S.group_first[tank + 1], sample, &wall_t);
         finish(rt, trt);
     }
+}
+
+// ---------------------------------------------------------------------------
+// Body update after the force pass (Eq. 20, Eq. 28, outputs): one warp per tank
+// ---------------------------------------------------------------------------
+// The kernel boundary after the force pass takes the place of a counter of
+// finished tiles: when the grid dependency resolves, every tile's sums are in
+// the tank's accumulators.  The previous body update and the call's run
+// record were complete before this kernel could be placed, so each warp loads
+// what the update reads (the body, the input, the controller) before the
+// dependency, and the update is one short chain after it.
+constexpr int kBodyWarps = 4;  // tanks per CTA
+
+__global__ void __launch_bounds__(32 * kBodyWarps) body_kernel(SimDev S, EvalOut E, int eval)
+{
+    pdl_trigger();
+    const int tank = blockIdx.x * kBodyWarps + (int)(threadIdx.x >> 5);
+    const int lane = (int)(threadIdx.x & 31);
+    if (tank >= S.B) return;  // a whole warp
+    const TankDev T = S.tank[tank];
+    const double pre = finalize_preload(S, T, tank);
+    const long long step = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 20));
+    pdl_wait();
+    BodyDev* bp = S.body + tank;
+    double vq = 0.0;
+    if (lane < 5) {  // each lane converts its own sum
+        vq = (double)(long long)__ldcg(&bp->acc[lane]) * kFixUnit;
+        bp->acc[lane] = 0ull;  // cleared for the next force pass
+    }
+    const double Fx = __shfl_sync(0xffffffffu, vq, 0), Fy = __shfl_sync(0xffffffffu, vq, 1);
+    const double Tq = __shfl_sync(0xffffffffu, vq, 2), Cx = __shfl_sync(0xffffffffu, vq, 3);
+    const double Cy = __shfl_sync(0xffffffffu, vq, 4);
+    const bool sample = !eval && (step % T.outer_every) == 0;
+    const F2 z{0.f, 0.f};
+    const Red none{z, z, z, z, z, 0ull};
+    tank_finalize(S, T, tank, eval, E, (int)(step & 1) ^ 1, step, sample, false, Fx, Fy, Tq, Cx, Cy, 0ull, none, pre);
 }
 
 // ---------------------------------------------------------------------------
@@ -1079,13 +1134,15 @@ static cudaError_t launch_tile_phase(const SimDev& S, const EvalOut& E, int eval
     if (tan) {
         if constexpr (TX * TY <= 32) {  // the tangent staging of 8x8 tiles exceeds static shared memory
             if (phase == 0) return launch(density_kernel<TX, TY, true>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+            if (phase == 2) return cudaSuccess;  // the tangent force pass updates the body itself
             return launch(force_kernel<TX, TY, true>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
         } else {
             return cudaErrorInvalidValue;
         }
     }
     if (phase == 0) return launch(density_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
-    return launch(force_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+    if (phase == 1) return launch(force_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+    return launch(body_kernel, (S.B + kBodyWarps - 1) / kBodyWarps, 32 * kBodyWarps, st, pdl, S, E, eval);
 }
 
 template <int TX, int TY>
@@ -1110,7 +1167,7 @@ void tile_dims(int code, int* tx, int* ty)
     *ty = T[code - 1][1];
 }
 
-// phase 0: density pass, phase 1: force pass
+// phase 0: density pass, 1: force pass, 2: body update (none in the tangent variant)
 cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, int phase,
                          cudaStream_t st, bool pdl, bool tan)
 {
@@ -1127,7 +1184,7 @@ cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_c
 cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, cudaStream_t st,
                         bool pdl, bool tan)
 {
-    for (int ph = 0; ph < 2; ++ph) {
+    for (int ph = 0; ph < 3; ++ph) {
         cudaError_t e = launch_phase(S, E, eval, tile_code, n_tiles, ph, st, pdl, tan);
         if (e != cudaSuccess) return e;
     }

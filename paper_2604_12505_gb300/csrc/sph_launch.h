@@ -13,6 +13,8 @@ size_t stage_record_bytes(const int* n_tiles);
 // pdl: launch with programmatic stream serialization (the kernels wait on
 // their predecessor with griddepcontrol before reading its results).
 // tan: the forward-mode tangent variants (tile codes 1..4 only).
+// Phases: 0 density pass, 1 force pass, 2 body update (the tangent variant's
+// force pass updates the body itself, its phase 2 launches nothing).
 cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, int phase,
                          cudaStream_t st, bool pdl, bool tan = false);
 cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, cudaStream_t st,

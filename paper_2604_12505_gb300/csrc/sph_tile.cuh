@@ -51,6 +51,7 @@ struct Stage {
     int slot[Sh::MAXS];
     unsigned char cell[Sh::MAXS];
     float2 rho[RHO ? Sh::MAXS : 1];
+    float2 vlo[RHO ? Sh::MAXS : 1];           // low parts (vx_lo, vy_lo) of the velocities (force pass)
     float4 tpv[TAN ? Sh::MAXS : 1];           // tangent (dx, dy, dvx, dvy)
     float2 trho[(TAN && RHO) ? Sh::MAXS : 1];  // tangent (d rho, d(P / rho^2))
 };
@@ -109,6 +110,17 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
         sm.own_row[TY] = acc;
     }
     const int total = sm.start[Sh::NC];
+    int own = 0;  // own particles (every thread from the scanned starts; thread 0 also writes own_row)
+    for (int r = 0; r < TY; ++r) own += sm.start[(r + 1) * Sh::SX + TX + 1] - sm.start[(r + 1) * Sh::SX + 1];
+    if (own == 0) {
+        // nothing to stage (the halo serves only the tile's own particles):
+        // the stage is left empty, every cell start 0, so that no caller
+        // reads staged particles that were not gathered
+        __syncthreads();  // every thread has read the starts
+        for (int c = tid; c <= Sh::NC; c += blockDim.x) sm.start[c] = 0;
+        __syncthreads();
+        return true;
+    }
     if (total > Sh::MAXS) {
         if (tid == 0) atomicOr(&S.body[S.tiles[blockIdx.x].x].flags, SPH_FLAG_STAGE_FULL);
         __syncthreads();
@@ -148,7 +160,10 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
         sm.pv[d] = S.pv[buf][gs];
         const float4 lo = S.lo[buf][gs];
         sm.plo[d] = make_float2(lo.x, lo.y);
-        if (RHO) sm.rho[d] = S.rhoP[gs];
+        if (RHO) {
+            sm.rho[d] = S.rhoP[gs];
+            sm.vlo[d] = make_float2(lo.z, lo.w);
+        }
         if constexpr (TAN) {
             sm.tpv[d] = S.tpv[buf][gs];
             if (RHO) sm.trho[d] = S.trho[gs];
@@ -241,6 +256,7 @@ __device__ __forceinline__ bool stage_from_record(const SimDev& S, int tank, int
             sm.pv[i] = S.pv[buf][gs];
             const float4 lo = S.lo[buf][gs];
             sm.plo[i] = make_float2(lo.x, lo.y);
+            sm.vlo[i] = make_float2(lo.z, lo.w);
             sm.rho[i] = S.rhoP[gs];
             if constexpr (TAN) {
                 sm.tpv[i] = S.tpv[buf][gs];

@@ -240,12 +240,13 @@ class Sim:
         return cell.value, W.value, G.value, (anc[0], anc[1])
 
     def time_kernels(self, n_steps: int, stream=None):
-        """Mean device time (us) of the density and force kernels over
-        n_steps zero-input steps, measured with CUDA events on the stream."""
-        us = (C.c_double * 2)()
+        """Mean device time (us) of the density, force and body-update
+        kernels over n_steps zero-input steps, measured with CUDA events on
+        the stream."""
+        us = (C.c_double * 3)()
         check(lib().sph_time_kernels(self._h, n_steps, us, _stream(stream)), "sph_time_kernels")
         self.steps_done += n_steps
-        return {"density": us[0], "force": us[1]}
+        return {"density": us[0], "force": us[1], "body": us[2]}
 
     def set_tile(self, code: int):
         check(lib().sph_set_tile(self._h, code), "sph_set_tile")
