@@ -587,6 +587,10 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     __shared__ GhostStage<!TAN> gs;
     __shared__ Red scratch[32];
     __shared__ int is_last;
+    // the successor is the body update, a few warps: placed at once, it
+    // prepares its update during this pass (the tangent variant's successor
+    // is the next density pass, placed after the loop as there)
+    if constexpr (!TAN) pdl_trigger();
     const int4 td = S.tiles[blockIdx.x];
     const int tank = td.x;
     const TankDev T = S.tank[tank];  // by value: the constants live in registers
@@ -814,7 +818,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         tacc.cx = F2{tcxs, 0.f};
         tacc.cy = F2{tcys, 0.f};
     }
-    pdl_trigger();  // past the particle loop (see the density pass)
+    if constexpr (TAN) pdl_trigger();  // past the particle loop (see the density pass)
     if (flags) atomicOr(&S.body[tank].flags, flags);
     if constexpr (!TAN) {
         // The tile's sums go into the tank's fixed-point accumulators by
@@ -913,22 +917,96 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
 // The kernel boundary after the force pass takes the place of a counter of
 // finished tiles: when the grid dependency resolves, every tile's sums are in
 // the tank's accumulators.  The previous body update and the call's run
-// record were complete before this kernel could be placed, so each warp loads
-// what the update reads (the body, the input, the controller) before the
-// dependency, and the update is one short chain after it.
+// record were complete before this kernel could be placed, so each warp does
+// everything that does not depend on this step's fluid force before the
+// dependency.  Kick then drift (Section 3.4) is affine in the fluid force and
+// torque: v' = v + dt (F + u) / M = A + B F, r' = r + dt v' = A' + B' F, and
+// likewise theta', thetadot' in T_b.  Lane l holds the coefficients of output
+// l, so after the dependency each output is one FP64 FMA (FP64 latency on this
+// GPU is 65 cycles per dependent operation), cos and sin of the new angle a
+// rotation by dtheta, and the lanes convert and store their own outputs.
+// Multiplication is reassociated against the oracle's sequence: the results
+// differ from it in the last bits only.
 constexpr int kBodyWarps = 4;  // tanks per CTA
+
+__device__ __forceinline__ double sel3(int i, double a, double b, double c) { return i == 0 ? a : (i == 1 ? b : c); }
 
 __global__ void __launch_bounds__(32 * kBodyWarps) body_kernel(SimDev S, EvalOut E, int eval)
 {
-    pdl_trigger();
     const int tank = blockIdx.x * kBodyWarps + (int)(threadIdx.x >> 5);
     const int lane = (int)(threadIdx.x & 31);
     if (tank >= S.B) return;  // a whole warp
     const TankDev T = S.tank[tank];
-    const double pre = finalize_preload(S, T, tank);
-    const long long step = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 20));
-    pdl_wait();
+    RunDev* run = S.run;
     BodyDev* bp = S.body + tank;
+    const double pre = finalize_preload(S, T, tank);
+    const double rx = __shfl_sync(0xffffffffu, pre, 0), ry = __shfl_sync(0xffffffffu, pre, 1);
+    const double th = __shfl_sync(0xffffffffu, pre, 2), vx = __shfl_sync(0xffffffffu, pre, 3);
+    const double vy = __shfl_sync(0xffffffffu, pre, 4), w = __shfl_sync(0xffffffffu, pre, 5);
+    double c = __shfl_sync(0xffffffffu, pre, 6), sn = __shfl_sync(0xffffffffu, pre, 7);
+    double tau_c = __shfl_sync(0xffffffffu, pre, 8);
+    const double ux = __shfl_sync(0xffffffffu, pre, 9), uy = __shfl_sync(0xffffffffu, pre, 10);
+    const double ut = __shfl_sync(0xffffffffu, pre, 11);
+    const double cJ = __shfl_sync(0xffffffffu, pre, 12), cw = __shfl_sync(0xffffffffu, pre, 13);
+    const double cxi = __shfl_sync(0xffffffffu, pre, 14), ref = __shfl_sync(0xffffffffu, pre, 15);
+    const long long sw = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 16));
+    double* const yout = (double*)__double_as_longlong(__shfl_sync(0xffffffffu, pre, 17));
+    const long long step0 = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 18));
+    const long long ystride = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 19));
+    const long long step = __double_as_longlong(__shfl_sync(0xffffffffu, pre, 20));
+    const bool ctrl_on = (sw & 1) != 0, body_fixed = (sw & 2) != 0;
+    const bool sample = !eval && (step % T.outer_every) == 0;
+    const int nbuf = (int)(step & 1) ^ 1;
+    double* y = nullptr;
+    if (sample) {
+        const long long oe = T.outer_every;
+        y = yout ? yout + tank * ystride + (step / oe - (step0 + oe - 1) / oe) * SPH_NY : nullptr;
+        if (ctrl_on) {  // Eq. 28 under zero-order hold, from the state before the step
+            const double Jc = cJ > 0.0 ? cJ : T.J_body;
+            tau_c = Jc * cw * cw * (ref - th) - 2.0 * cxi * Jc * cw * w;
+            if (lane == 0) bp->tau_c = tau_c;
+        }
+        if (y && lane < 6) y[lane] = pick(lane, 0, rx, ry, th, vx, vy, w);
+    }
+    const double tau = ut + (ctrl_on ? tau_c : 0.0);
+    // output l = A + B F_which: 0..5 r', theta', rdot', thetadot'; 6, 7 r' - W
+    // (the origin of the next grid); in an evaluation 0..5 are F_b, T_b and
+    // the accelerations of Eq. 20
+    const double dt = T.dt_d, im = T.inv_m_body, iJ = T.inv_J_body;
+    const int comp = lane % 3;  // F_x, F_y or T_b for lanes 0..7 (0, 1, 2, 0, 1, 2, 0, 1)
+    const int k = lane < 8 ? lane : 0;
+    double A, B;
+    if (eval) {
+        const double u3 = sel3(comp, ux, uy, tau), i3 = comp == 2 ? iJ : im;
+        A = k < 3 ? 0.0 : u3 * i3;
+        B = k < 3 ? 1.0 : i3;
+    } else if (body_fixed) {
+        A = pick(k, 0, rx, ry, th, vx, vy, w, rx - T.W, ry - T.W);
+        B = 0.0;
+    } else {
+        const double x0 = sel3(comp, rx, ry, th), v0 = sel3(comp, vx, vy, w);
+        const double u3 = sel3(comp, ux, uy, tau), i3 = comp == 2 ? iJ : im;
+        const double Av = v0 + dt * (u3 * i3), Bv = dt * i3;  // velocity
+        const bool vel = (k >= 3 && k <= 5);
+        A = vel ? Av : x0 + dt * Av - (k >= 6 ? T.W : 0.0);
+        B = vel ? Bv : dt * Bv;
+    }
+    // rotation of (cos, sin) by dtheta = dt thetadot' = Ad + Bd T_b, with
+    // (cos, sin) first brought back to unit norm (off the dependent chain)
+    double Ad = 0.0, Bd = 0.0;
+    if (!eval && !body_fixed) {
+        Ad = dt * (w + dt * (tau * iJ));
+        Bd = dt * dt * iJ;
+        const double f = 1.5 - 0.5 * (c * c + sn * sn);
+        c *= f;
+        sn *= f;
+    }
+    const double X = lane == 9 ? sn : c, Yr = lane == 9 ? c : -sn;  // lane 8: cos', lane 9: sin'
+
+    pdl_wait();
+    // the next density pass may be placed now: every tile of the force pass
+    // has finished, so its CTAs take no SM slot that this step still needs
+    pdl_trigger();
     double vq = 0.0;
     if (lane < 5) {  // each lane converts its own sum
         vq = (double)(long long)__ldcg(&bp->acc[lane]) * kFixUnit;
@@ -937,10 +1015,66 @@ __global__ void __launch_bounds__(32 * kBodyWarps) body_kernel(SimDev S, EvalOut
     const double Fx = __shfl_sync(0xffffffffu, vq, 0), Fy = __shfl_sync(0xffffffffu, vq, 1);
     const double Tq = __shfl_sync(0xffffffffu, vq, 2), Cx = __shfl_sync(0xffffffffu, vq, 3);
     const double Cy = __shfl_sync(0xffffffffu, vq, 4);
-    const bool sample = !eval && (step % T.outer_every) == 0;
-    const F2 z{0.f, 0.f};
-    const Red none{z, z, z, z, z, 0ull};
-    tank_finalize(S, T, tank, eval, E, (int)(step & 1) ^ 1, step, sample, false, Fx, Fy, Tq, Cx, Cy, 0ull, none, pre);
+    const double lin = fma(B, sel3(comp, Fx, Fy, Tq), A);
+    double v = lin;
+    if (!eval && !body_fixed) {
+        const double d = fma(Bd, Tq, Ad), d2 = d * d;
+        double cd, sd;
+        if (fabs(d) <= 1e-4) {  // first omitted terms d^4 / 24, d^5 / 120 below 1e-16 relative
+            cd = fma(-0.5, d2, 1.0);
+            sd = fma(d * d2, -1.0 / 6.0, d);
+        } else if (fabs(d) <= 1e-2) {
+            cd = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0 - d2 * (1.0 / 720.0)));
+            sd = d * (1.0 - d2 * (1.0 / 6.0 - d2 * (1.0 / 120.0 - d2 * (1.0 / 5040.0))));
+        } else {
+            double s1, c1;
+            sincos(d, &s1, &c1);
+            cd = c1;
+            sd = s1;
+        }
+        if (lane == 8 || lane == 9) v = fma(X, cd, Yr * sd);
+    } else if (lane == 8 || lane == 9) {
+        v = X;  // unchanged angle
+    }
+    if (sample && y && lane >= 6 && lane < SPH_NY) {
+        double o = sel3(lane - 6, Fx, Fy, Tq);
+        if (lane == 9) o = T.n_f ? Cx / T.n_f : 0.0;
+        if (lane == 10) o = T.n_f ? Cy / T.n_f : 0.0;
+        y[lane] = o;
+    }
+    if (eval) {
+        if (E.body && lane < 6) E.body[6 * tank + lane] = v;
+    } else {
+        if (lane < 2) bp->anchor[nbuf][lane] = lane ? ry : rx;  // the state before the step
+        // the leading doubles of BodyDev: r, theta, rdot, thetadot (lanes 0-5), cos, sin (lanes 8, 9)
+        if (!body_fixed && (lane < 6 || lane == 8 || lane == 9)) reinterpret_cast<double*>(bp)[lane < 6 ? lane : lane - 2] = v;
+        // FP32 forms: two-float splits (dc, ds from lanes 8, 9; drx, dry from
+        // 0, 1), rounded values (fc, fs; frx, fry; fo_next from 6, 7; fvx, fvy, fw from 3-5)
+        const float hi = (float)v;
+        const float lo = (float)(v - (double)hi);
+        if (lane == 8 || lane == 9) {
+            (&bp->dc)[lane - 8] = make_float2(hi, lo);
+            (&bp->fc)[lane - 8] = hi;
+        } else if (lane < 2) {
+            (&bp->drx)[lane] = make_float2(hi, lo);
+            (&bp->frx)[lane] = hi;
+        } else if (lane == 6 || lane == 7) {
+            bp->fo_next[lane - 6] = hi;
+        } else if (lane >= 3 && lane < 6) {
+            (&bp->fvx)[lane - 3] = hi;
+        }
+    }
+    if (lane != 0) return;
+    if (S.B == 1) {  // the only tank: its step is the pass's (visible when the kernel completes)
+        if (!eval) run->step = step + 1;
+        return;
+    }
+    fence_acq_rel();
+    const unsigned prev = atomicAdd(&run->tanks_done, 1u);
+    if (prev == (unsigned)S.B - 1) {
+        if (!eval) run->step = step + 1;
+        run->tanks_done = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
