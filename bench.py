@@ -130,11 +130,14 @@ def _peaks():
 # data structures the kernel must read or write once):
 #   density  per particle 28 B (16 pv + 4 index + 8 rho/P out) + per cell 8 B (count read, next count clear)
 #            + per ghost 48 B (16 body-frame position in, 32 world position / velocity out)
+#            + per particle 16 B (the low words of the two-float position and velocity, read)
 #   force    per particle 52 B (16 pv + 4 index + 8 rho/P in; 16 pv + 4 index out; 4 count claim)
-#            + per cell 4 B + per ghost 32 B
+#            + per particle 32 B (low words read and written) + per cell 4 B + per ghost 32 B
+#   body     per tank 5 x 8 B fixed-point sums read and cleared, 8 x 8 B body state read and
+#            written, 11 x 8 B sample: under 0.5 KB, independent of the particle count
 def algorithmic_bytes(n_f, n_g, n_cells):
-    return {"density": 28 * n_f + 8 * n_cells + 48 * n_g,
-            "force": 52 * n_f + 4 * n_cells + 32 * n_g}
+    return {"density": 44 * n_f + 8 * n_cells + 48 * n_g,
+            "force": 84 * n_f + 4 * n_cells + 32 * n_g}
 
 
 # Algorithmic FP32 operations of one force launch, counted from the kernel's
@@ -149,14 +152,25 @@ def algorithmic_flop_force(n_ff, n_fg, n_f):
     return 35 * n_ff + 40 * n_fg + 18 * n_f
 
 
+# Algorithmic FP32 operations of one density launch (FMA counts two):
+#   fluid pair within 2h, the particle itself included (Eq. 14)   22: two-word separation 6,
+#                                     r^2 3, rsqrt 1, q 2, 2 - q 1, max(1 - q, 0) 2, bracket 6, sum 1
+#   ghost within 2h (Eq. 14)          20: two-word separation 6, r^2 3, rsqrt 1, r 1, kernel 8, sum 1
+#   particle (Eqs. 14, 11)            9: scale 1, gamma1 sum 2, EOS 2, P / rho^2 3, store conversion 1
+# The pass evaluates the bracket for every candidate of the clipped stencil
+# (branch-free); only the pairs inside the support are counted here.
+def algorithmic_flop_density(n_ff, n_fg2, n_f):
+    return 22 * (n_ff + n_f) + 20 * n_fg2 + 9 * n_f
+
+
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 FLOP per FMA x SM clock.
 FP32_LANES = 152 * 128
 
-# DRAM bytes (read + write) per launch of force_kernel on the large tank, by
-# tile code, mean of three launches captured warm (ncu --cache-control none):
-# the working set stays in L2.  Valid for the kernel source they were
-# captured on; a tile without a capture reports null.
-FORCE_TRAFFIC_BYTES = {4: 47_104}
+# DRAM bytes (read + write) per launch on the large tank, by kernel and tile
+# code, mean of three launches captured warm (ncu --cache-control none): the
+# working set stays in L2.  Valid for the kernel source they were captured
+# on; a kernel or tile without a capture of the current source reports null.
+TRAFFIC_BYTES: dict[tuple[str, int], int] = {}
 
 
 # --------------------------------------------------------------------------
@@ -244,7 +258,8 @@ def surrogate(size: str) -> dict:
     t0 = time.perf_counter()
     r = pipeline.surrogate_study(**kw)
     cl, th, ds = r["closed_loop_lpv"], r["throughput"], r["dataset"]
-    short = lambda c: {"attitude": c["nrmse_attitude"], "translation": c["nrmse_translation"], "mean": c["nrmse_mean"]}
+    short = lambda c: {"attitude": c["nrmse_attitude"], "translation": c["nrmse_translation"], "mean": c["nrmse_mean"],
+                       "all_channels_within_5pct": c["all_channels_within_5pct"]}
     return {
         "size": size,
         "surrogate_sims_per_s": th["surrogate_sims_per_s"], "sph_sims_per_s": th["sph_sims_per_s"],
@@ -257,8 +272,10 @@ def surrogate(size: str) -> dict:
                         "sph_s": th["sph_s"]},
         "dataset": {k: ds[k] for k in ("trajectories", "samples", "tanks", "particles", "batched_ms_per_step",
                                        "sequential_ms_per_step", "batched_speedup", "sequential_sample")},
-        "fit": {"lpv": {k: r["fit_lpv"][k] for k in ("train_loss", "seconds")},
-                "lti": {k: r["fit_lti"][k] for k in ("train_loss", "seconds")}},
+        "fit": {"lpv": {k: r["fit_lpv"][k] for k in ("train_loss", "seconds", "test_nrmse_outputs")},
+                "lti": {k: r["fit_lti"][k] for k in ("train_loss", "seconds", "test_nrmse_outputs")}},
+        "output_channels": ["F_b,x", "F_b,y", "T_b", "fluid CoM offset"],
+        "scheduling": r["scheduling"],
         "wall_s": time.perf_counter() - t0,
     }
 
@@ -405,23 +422,30 @@ def run_ours(a):
     cell, Wd, G, _ = sim.grid_info(0)
     ab = algorithmic_bytes(sim.n_fluid[0], sim.n_ghost[0], G * G)
     nbr = sim.eval()["nbr"].cpu().numpy().astype(np.int64)
-    flop = algorithmic_flop_force(int(nbr[:, 0].sum()), int(nbr[:, 2].sum()), sim.n_fluid[0])
-    dom = max(kt, key=kt.get)
+    flop = {"force": algorithmic_flop_force(int(nbr[:, 0].sum()), int(nbr[:, 2].sum()), sim.n_fluid[0]),
+            "density": algorithmic_flop_density(int(nbr[:, 0].sum()), int(nbr[:, 1].sum()), sim.n_fluid[0])}
     peaks, peak_src = _peaks()
     sm_mhz = clk.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-    gbs = ab["force"] / (kt["force"] * 1e-6) / 1e9
-    tflops = flop / (kt["force"] * 1e-6) / 1e12
-    # the force kernel dominates; its intensity (flop / algorithmic bytes) is
-    # above this GPU's FP32 ridge and its data stay in L2: FP32-ALU roofline
-    roof = {"bound": "alu", "kernel": "force_kernel", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-            "frac": tflops / fp32_peak,
-            "traffic": FORCE_TRAFFIC_BYTES.get(tile),
-            "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
-            "algorithmic_flop": flop, "intensity_flop_per_byte": flop / ab["force"],
-            "kernel_us": kt, "dominant": f"{dom}_kernel",
-            "hbm_view": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
-                         "algorithmic_bytes": ab["force"], "peak_source": f"{peak_src} hbm_gbs"}}
+
+    def kernel_roof(name):
+        gbs = ab[name] / (kt[name] * 1e-6) / 1e9
+        tflops = flop[name] / (kt[name] * 1e-6) / 1e12
+        # both tile passes have intensities near or above this GPU's FP32
+        # ridge and keep their data in L2: FP32-ALU roofline, HBM view beside
+        return {"bound": "alu", "kernel": f"{name}_kernel", "achieved": tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": tflops / fp32_peak, "traffic": TRAFFIC_BYTES.get((name, tile)),
+                "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz (median SM clock under load)",
+                "algorithmic_flop": flop[name], "intensity_flop_per_byte": flop[name] / ab[name],
+                "launch_us": kt[name],
+                "hbm_view": {"achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"], "frac": gbs / peaks["hbm_gbs"],
+                             "algorithmic_bytes": ab[name], "peak_source": f"{peak_src} hbm_gbs"}}
+
+    # the dominant kernel by its serial launch time (sph_time_kernels)
+    dom = max(("density", "force"), key=lambda k: kt[k])
+    roof = kernel_roof(dom)
+    roof["kernel_us"] = kt
+    roof["other"] = kernel_roof("force" if dom == "density" else "density")
 
     if rank != 0:
         return
@@ -432,7 +456,7 @@ def run_ours(a):
         "config": dict(desc, parallelism="replicas" if world > 1 else "single", tile=tile,
                        autotune_us_per_step=tune_us),
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": K * (2 * inner + 1),
+        "gpu_launches": K * (3 * inner + 1),   # per sph_step call: the run setup, then density, force, body per step
         "roofline": roof,
         "clocks": clk,
         "us_per_inner_step": 1e6 * T / (K * inner),

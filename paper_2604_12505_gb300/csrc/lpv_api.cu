@@ -5,6 +5,7 @@
 #include <cstring>
 #include <random>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/lpv.h"
@@ -415,50 +416,98 @@ int lpv_fit(const float* u, const float* y, const float* p, int32_t n_traj, int3
     lpv_model* M = nullptr;
     int rc = lpv_create(cfg, &M);
     if (rc) return rc;
+    const int restarts = cfg->restarts > 0 ? cfg->restarts : 1;
+    std::vector<lpv_model*> R(restarts, nullptr);
+    std::vector<cudaStream_t> S(restarts, nullptr);
     auto bail = [&](int code) {
+        std::string msg = sph_last_error();
+        for (int r = 0; r < restarts; ++r) {
+            if (S[r]) cudaStreamDestroy(S[r]);
+            lpv_destroy(R[r]);
+        }
         lpv_destroy(M);
-        return code;
+        return err(code, msg);
     };
     if ((rc = lpv_normalize(M, u, y, p, n_traj, T, stream))) return bail(rc);
     if ((rc = lpv_init_ls(M, u, y, n_traj, T, nullptr, stream))) return bail(rc);
     const Dims& d = M->d;
     const int nr = d.nx + d.ny, nc = d.nx + d.nu, nw = d.nkt * nr * nc;
-    std::vector<float> W0(nw), W(nw), Wbest(nw);
+    std::vector<float> W0(nw);
     if ((rc = lpv_get_params(M, W0.data(), nullptr))) return bail(rc);
-    double best = INFINITY;
-    const int restarts = cfg->restarts > 0 ? cfg->restarts : 1;
+    // The restarts are independent: each gets a model of its own, a stream of
+    // its own and a host thread that drives its Adam and L-BFGS loops, so
+    // that their launches (a few dozen warps each) fill the GPU together and
+    // the line searches' host round trips overlap.  Every restart computes
+    // exactly what it would alone, so the best one is the same as in a
+    // sequential loop.
+    std::vector<std::vector<float>> Wr(restarts, W0);
     for (int r = 0; r < restarts; ++r) {
         // M_0 from the least-squares fit; the B and C blocks of M_i ~ N(0,
         // init_scale^2) (Section 5.3.2), their A blocks 0 so that A(p) = A_0
         // keeps the stable spectrum of the start for every p
         std::mt19937_64 gen(cfg->seed + 1000003ull * (uint64_t)r);
         std::normal_distribution<double> nd(0.0, cfg->init_scale);
-        W = W0;
         for (int i = nr * nc; i < nw; ++i) {
             const int o = (i / nc) % nr, f = i % nc;
             const double draw = nd(gen);
-            W[i] = (o < d.nx && f < d.nx) ? 0.f : (float)draw;
+            Wr[r][i] = (o < d.nx && f < d.nx) ? 0.f : (float)draw;
         }
-        if ((rc = lpv_set_params(M, W.data(), nullptr))) return bail(rc);
-        if ((rc = lpv_train(M, u, y, p, n_traj, T, cfg->adam_iters, nullptr, stream))) return bail(rc);
-        if (cfg->lbfgs_iters > 0) {
-            rc = lpv_lbfgs(M, u, y, p, n_traj, T, cfg->lbfgs_iters, nullptr, stream);
-            if (rc == SPH_E_DIVERGED) continue;  // this restart ended with a non-finite loss
-            if (rc) return bail(rc);
-        }
-        double L = 0.0;
-        if ((rc = lpv_loss_grad(M, u, y, p, n_traj, T, &L, nullptr, stream))) return bail(rc);
-        if (L < best) {
-            best = L;
-            if ((rc = lpv_get_params(M, Wbest.data(), nullptr))) return bail(rc);
+        if ((rc = lpv_create(cfg, &R[r]))) return bail(rc);
+        R[r]->d = M->d;  // the normalisation of the data, exactly
+        if ((rc = lpv_set_params(R[r], Wr[r].data(), nullptr))) return bail(rc);
+        if (cudaStreamCreateWithFlags(&S[r], cudaStreamNonBlocking) != cudaSuccess) {
+            S[r] = nullptr;
+            return bail(err(SPH_E_CUDA, "lpv_fit: cudaStreamCreate failed"));
         }
     }
-    if (!std::isfinite(best)) {
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)  // the data are complete before other streams read them
+        return bail(err(SPH_E_CUDA, "lpv_fit: cudaStreamSynchronize failed"));
+    std::vector<int> codes(restarts, SPH_OK);
+    std::vector<double> loss(restarts, INFINITY);
+    std::vector<std::string> msgs(restarts);
+    {
+        std::vector<std::thread> th;
+        th.reserve(restarts);
+        for (int r = 0; r < restarts; ++r)
+            th.emplace_back([&, r] {
+                lpv_model* m = R[r];
+                void* st = (void*)S[r];
+                int c = lpv_train(m, u, y, p, n_traj, T, cfg->adam_iters, nullptr, st);
+                if (!c && cfg->lbfgs_iters > 0) c = lpv_lbfgs(m, u, y, p, n_traj, T, cfg->lbfgs_iters, nullptr, st);
+                double L = INFINITY;
+                if (!c) c = lpv_loss_grad(m, u, y, p, n_traj, T, &L, nullptr, st);
+                codes[r] = c;
+                loss[r] = c ? INFINITY : L;
+                if (c) msgs[r] = sph_last_error();
+            });
+        for (auto& t : th) t.join();
+    }
+    int best_r = -1;
+    for (int r = 0; r < restarts; ++r) {
+        if (codes[r] == SPH_E_DIVERGED) continue;  // this restart ended with a non-finite loss
+        if (codes[r]) {
+            err(codes[r], msgs[r]);
+            return bail(codes[r]);
+        }
+        if (!std::isfinite(loss[r])) continue;
+        if (best_r < 0 || loss[r] < loss[best_r]) best_r = r;  // first of equal losses, as in order
+    }
+    if (best_r < 0) {
+        err(SPH_E_DIVERGED, "lpv_fit: no restart ended with a finite training loss");
+        return bail(SPH_E_DIVERGED);
+    }
+    std::vector<float> Wbest(nw);
+    if ((rc = lpv_get_params(R[best_r], Wbest.data(), nullptr))) return bail(rc);
+    for (int r = 0; r < restarts; ++r) {
+        cudaStreamDestroy(S[r]);
+        lpv_destroy(R[r]);
+    }
+    if ((rc = lpv_set_params(M, Wbest.data(), nullptr))) {
+        std::string msg = sph_last_error();
         lpv_destroy(M);
-        return err(SPH_E_DIVERGED, "lpv_fit: no restart ended with a finite training loss");
+        return err(rc, msg);
     }
-    if ((rc = lpv_set_params(M, Wbest.data(), nullptr))) return bail(rc);
-    if (best_loss) *best_loss = best;
+    if (best_loss) *best_loss = loss[best_r];
     *out = M;
     return SPH_OK;
 }

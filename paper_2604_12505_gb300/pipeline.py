@@ -151,13 +151,43 @@ def identification_inputs(B: int, K: int, Ts: float, seed0: int) -> np.ndarray:
                                             pulse_rest=(1.0 * scale, 4.0 * scale)) for b in range(B)])
 
 
+def scheduling_use(model, u, y, p, train) -> dict:
+    """Whether a fitted LPV model (Eq. 24, p = [fill, thetadot]) uses its
+    scheduling: the Frobenius norm of each M_i (i >= 1) and of its A, B and C
+    blocks relative to M_0's, and the held-out open-loop output NRMSE of the
+    model as fitted, with p frozen at its training mean, and with one
+    channel of p frozen at a time."""
+    W = model.get_params()[0].astype(np.float64)
+    c = model.cfg
+    nx = c["n_x"]
+    blocks = dict(A=(slice(0, nx), slice(0, nx)), B=(slice(0, nx), slice(nx, None)),
+                  C=(slice(nx, None), slice(0, nx)))
+    rel = lambda a, b: float(np.linalg.norm(a) / max(np.linalg.norm(b), 1e-300))
+    norms = {f"M{i}": dict(all=rel(W[i], W[0]), **{k: rel(W[i][r, q], W[0][r, q]) for k, (r, q) in blocks.items()})
+             for i in range(1, W.shape[0])}
+    pt, pm = p[~train][:, :, :c["n_p"]], p[train][:, :, :c["n_p"]].reshape(-1, c["n_p"]).mean(axis=0)
+    yt, ut = y[~train], u[~train]
+
+    def held_out(pp):
+        yh = model.predict(ut, pp).cpu().numpy()
+        return np.mean([nrmse(a, b) for a, b in zip(yt, yh)], axis=0).tolist()
+
+    frozen = dict(fitted=held_out(pt), all_frozen=held_out(np.broadcast_to(pm, pt.shape).copy()))
+    for j, name in enumerate(["fill", "thetadot"][:c["n_p"]]):
+        q = pt.copy()
+        q[:, :, j] = pm[j]
+        frozen[f"{name}_frozen"] = held_out(q)
+    return dict(weight_norm_vs_M0=norms, p_train_mean=pm.tolist(), held_out_output_nrmse=frozen)
+
+
 def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, relax: int = 5000,
                     dt: float = 2e-4, cl_tanks: int = 64, cl_steps: int = 5000, n_sims: int = 65_536,
                     fit_cfg: dict | None = None, seq_tanks: int | None = None, seq_steps: int = 200, ctrl=None,
-                    log=None, inputs: str = "piecewise") -> dict:
+                    log=None, inputs: str = "piecewise", fill=(0.2, 0.8), dx=(0.004, 0.01)) -> dict:
     """The surrogate workflow on the simulator and the LPV library.
 
-    1. D_N: n_tanks tanks (fill, dx from the data-set distribution) relaxed
+    1. D_N: n_tanks tanks (fill ~ U[fill], dx ~ U[dx]: a degenerate range
+       such as dx=(0.006, 0.006) gives tanks that differ only in fill) relaxed
        once, ``launches`` open-loop runs of ``steps`` steps each with seeded
        inputs -- piecewise-constant holds (``inputs="piecewise"``) or the
        identification train scaled to the horizon (``inputs="train"``); the
@@ -176,7 +206,7 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
     say = log or (lambda *a: None)
     ctrl = ctrl or dict(omega=0.2 * np.pi, xi=0.7)
     out: dict = {}
-    params = [dict(p, dt=dt) for p in W.batch_tank_params(n_tanks, seed0=1000)]
+    params = [dict(p, dt=dt) for p in W.batch_tank_params(n_tanks, seed0=1000, fill=fill, dx=dx)]
     outer = params[0]["outer_every"]
     Ts = dt * outer
     K = steps // outer
@@ -225,8 +255,10 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
         fits[name] = model
         out[f"fit_{name}"] = dict(train_loss=best, seconds=fit_s, test_nrmse_outputs=e.tolist())
         say("fit", name, out[f"fit_{name}"])
+    out["scheduling"] = scheduling_use(fits["lpv"], u, y, p, tr)
+    say("scheduling", out["scheduling"])
 
-    pt = [dict(q, dt=dt) for q in W.batch_tank_params(cl_tanks, seed0=2000)]
+    pt = [dict(q, dt=dt) for q in W.batch_tank_params(cl_tanks, seed0=2000, fill=fill, dx=dx)]
     Kc = cl_steps // outer
     F, tau, ref = _closed_loop_inputs(cl_tanks, Kc, Ts, seed0=200_000)
     tt = Tanks(pt, relax)
@@ -253,7 +285,8 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
     for name, m in (("lpv", fits["lpv"]), ("lti", lti), ("no_fluid", none)):
         per, att, trn = cl_err(m)
         out[f"closed_loop_{name}"] = dict(nrmse=per, nrmse_attitude=att, nrmse_translation=trn,
-                                          nrmse_mean=float(np.mean(list(per.values()))))
+                                          nrmse_mean=float(np.mean(list(per.values()))),
+                                          all_channels_within_5pct=bool(max(per.values()) <= 0.05))
         say("closed loop", name, out[f"closed_loop_{name}"])
 
     # throughput: n_sims surrogate runs (the held-out manoeuvres tiled), inputs resident
@@ -345,7 +378,7 @@ def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int 
     copies with their own spawns and inputs stepped together.  The health flags (SPH_FLAG_*)
     after the relaxation and after each flight are recorded; a gamma1 whose
     relaxation already lets fluid through the wall is not flown.  `extra`
-    (e.g. dict(ghost_pressure_clamp=1), reading R34) is applied to Table 2's
+    (e.g. dict(ghost_pressure_clamp=1): Eq. 16 with max(P_i, 0)) is applied to Table 2's
     walls."""
     from . import workloads as W
     from .sph import Sim, gamma1_estimate
@@ -432,8 +465,17 @@ def paper_scenario_study(seconds: float = 30.0, relax: int = 20_000, batch: int 
             e1.record()
             torch.cuda.synchronize()
             tb = e0.elapsed_time(e1) * 1e-3
+            xv, body = sim.state()
+            lim = base["R"] + (cfg["n_rings"] - 0.5) * cfg["ghost_spacing"] * base["dx"]
+            o, past = 0, []
+            for b, n in enumerate(sim.n_fluid):
+                d = (xv[o:o + n, :2].double() - body[b, :2]).norm(dim=1)
+                past.append(int((~(d <= lim)).sum().item()))
+                o += n
             run["batch"] = dict(tanks=batch, device_s=tb, flights_per_s=batch / tb, relax_flags=bflags,
-                                flight_flags=sim.check(reset=True, raise_on_error=False))
+                                flight_flags=sim.check(reset=True, raise_on_error=False),
+                                tanks_past_ghosts=int(sum(q > 0 for q in past)),
+                                particles_past_ghosts=int(sum(past)))
         run["speedup_vs_paper_one_tank"] = out["paper"]["profile1_s"] * (seconds / 30.0) / run["one_tank_wall_s"]
         say("paper scenario", run)
         out["runs"].append(run)
@@ -568,11 +610,19 @@ if __name__ == "__main__":
     if len(sys.argv) > 1 and sys.argv[1] == "linearize":
         print(json.dumps(linearization_study(log=lambda *a: print(*a, file=sys.stderr))))
     elif len(sys.argv) > 1 and sys.argv[1] == "paper":
-        # "paper clamp": Table 2's walls with reading R34 (Eq. 16 with max(P_i, 0))
+        # "paper clamp": Table 2's walls with Eq. 16 taking max(P_i, 0)
         extra = dict(ghost_pressure_clamp=1) if "clamp" in sys.argv[2:] else None
         print(json.dumps(paper_scenario_study(extra=extra, log=lambda *a: print(*a, file=sys.stderr))))
+    elif len(sys.argv) > 1 and sys.argv[1] == "surrogate":
+        # "surrogate fill_only": the data-set workload with every tank at dx = 6 mm
+        kw = dict(fit_cfg=dict(adam_iters=2000, restarts=8, lbfgs_iters=100), seq_tanks=8)
+        if "fill_only" in sys.argv[2:]:
+            kw["dx"] = (0.006, 0.006)
+        r = surrogate_study(**kw, log=lambda *a: print(*a, file=sys.stderr))
+        print(json.dumps(r))
     elif len(sys.argv) > 1 and sys.argv[1] == "velocity":
         print(json.dumps(velocity_surrogate_study(log=lambda *a: print(*a, file=sys.stderr))))
     else:
-        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper [clamp]|velocity", file=sys.stderr)
+        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper [clamp]|surrogate [fill_only]|velocity",
+              file=sys.stderr)
         sys.exit(2)

@@ -289,3 +289,25 @@ def test_fit_with_lbfgs_ends_no_worse_than_adam_alone():
     _, best_adam = lpv.fit(u, y, p, cfg)
     _, best_both = lpv.fit(u, y, p, dict(cfg, lbfgs_iters=50))
     assert np.isfinite(best_both) and best_both <= best_adam
+
+
+def test_concurrent_restarts_equal_the_restarts_run_alone():
+    # The restarts of lpv_fit run concurrently (a model, a stream and a host
+    # thread each).  Restart r draws its M_i from the seed + 1000003 r, so a
+    # fit with one restart and that seed is restart r alone: the best loss
+    # of the concurrent fit is the least of those, bit for bit, and its
+    # weights are that restart's weights.
+    need_gpu()
+    from paper_2604_12505_gb300 import lpv
+    rng = np.random.default_rng(9)
+    Wt = _stable_W(rng)
+    u, p = _data(rng, 40, 50)
+    y = np.stack([L.simulate(Wt, u[b], p[b], NX)[0] for b in range(40)])
+    cfg = dict(adam_iters=60, lbfgs_iters=20, lr=3e-3, sigma2=1e-6, init_scale=0.05, seed=11)
+    model, best = lpv.fit(u, y, p, dict(cfg, restarts=4))
+    alone = [lpv.fit(u, y, p, dict(cfg, restarts=1, seed=11 + 1000003 * r)) for r in range(4)]
+    losses = [b for _, b in alone]
+    assert len(set(losses)) > 1
+    r = int(np.argmin(losses))
+    assert best == losses[r]
+    np.testing.assert_array_equal(model.get_params()[0], alone[r][0].get_params()[0])

@@ -22,7 +22,7 @@ def test_cubic_normalised_with_reading_constant(orc, h):
 
 
 def test_cubic_printed_constant_integrates_to_three(orc):
-    # The constant printed in Eq. 22, 15/(14 pi), gives 3: the reason for reading R1.
+    # The constant printed in Eq. 22, 15/(14 pi), gives 3, so the normalised kernel takes 5/(14 pi).
     h = 0.7
     assert _radial_integral(lambda r: orc.w_cubic(r, h, 15.0 / (14.0 * math.pi)), 2 * h) == pytest.approx(3.0, abs=1e-10)
 
