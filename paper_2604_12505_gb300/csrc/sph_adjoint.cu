@@ -185,11 +185,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_force_kernel(SimDe
                 xbx += k1 * dax + k2 * dx + k3 * (ux - k4 * dx);
                 xby += k1 * day + k2 * dy + k3 * (uy - k4 * dy);
             };
-            const int nn = t < Sh::MAXOWN ? (int)S.nbn[blockIdx.x * Sh::MAXOWN + t] : 255;
-            if (nn <= kNbrMax) {
-                const unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
-                for (int k = 0; k < nn; ++k) pair(lst[k * Sh::MAXOWN]);
-            } else {
+            if (!for_recorded_neighbours<Sh::MAXOWN>(S, blockIdx.x, t, pair)) {
                 const int c = sm.cell[e];
 #pragma unroll
                 for (int dyc = -1; dyc <= 1; ++dyc) {
@@ -289,11 +285,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS) adj_density_kernel(Sim
                 xbx += k * dx;
                 xby += k * dy;
             };
-            const int nn = t < Sh::MAXOWN ? (int)S.nbn[blockIdx.x * Sh::MAXOWN + t] : 255;
-            if (nn <= kNbrMax) {
-                const unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
-                for (int k = 0; k < nn; ++k) pair(lst[k * Sh::MAXOWN]);
-            } else {
+            if (!for_recorded_neighbours<Sh::MAXOWN>(S, blockIdx.x, t, pair)) {
                 const int c = sm.cell[e];
 #pragma unroll
                 for (int dyc = -1; dyc <= 1; ++dyc) {

@@ -226,7 +226,8 @@ void free_sim(sph_sim* s)
     cudaFree(s->S.rhoP);
     cudaFree(s->S.partials);
     cudaFree(s->S.gpartials);
-    cudaFree(s->S.nbl);
+    cudaFree(s->S.nbm);
+    cudaFree(s->S.nba);
     cudaFree(s->S.nbn);
     cudaFree(s->S.srec);
     for (int b = 0; b < 2; ++b) cudaFree(s->S.tpv[b]);
@@ -442,15 +443,15 @@ int create_impl(const sph_params* p, int B, cudaStream_t st, sph_sim** out)
     s->max_groups = max_groups;
     rc |= dalloc(&s->S.partials, max_tiles);
     rc |= dalloc(&s->S.gpartials, max_groups);
-    {   // neighbour lists: per tile kNbrMax x (TX*TY*12) entries, sized for the largest shape
-        size_t nb = 0, nn = 0;
+    {   // neighbour records: per tile 3 rows x (TX*TY*12) own particles, sized for the largest shape
+        size_t nn = 0;
         for (int code = 1; code <= SPH_TILE_COUNT; ++code) {
             int TX, TY;
             tile_dims(code, &TX, &TY);
             nn = std::max(nn, (size_t)s->n_tiles[code] * TX * TY * 12);
         }
-        nb = nn * kNbrMax;
-        rc |= dalloc(&s->S.nbl, nb);
+        rc |= dalloc(&s->S.nbm, 3 * nn);
+        rc |= dalloc(&s->S.nba, 3 * nn);
         rc |= dalloc(&s->S.nbn, nn);
     }
     rc |= dalloc(&s->S.gdone, max_groups);

@@ -201,7 +201,8 @@ struct __align__(16) TilePartial {
 
 constexpr int kTileGroup = 64;    // tiles per first-level reduction group
 constexpr int kOneLevelLoads = 8; // one-level reduction up to this many partials per thread of a tile
-constexpr int kNbrMax = 40;       // fluid neighbours recorded per particle by the density pass
+constexpr int kNbrRowBits = 32;   // candidates of one stencil row the density pass can record as a bit mask
+constexpr unsigned char kNbrNone = 255;  // neighbour count marking a particle whose rows were not recorded
 
 // Optional per-particle outputs of an evaluation pass (indexed by particle).
 struct EvalOut {
@@ -235,8 +236,9 @@ struct SimDev {
     const int* gstart;            // per tank (G*G + 1) ghost-cell starts (global ghost index)
     float4* gpos;                 // per step: (hi_x, hi_y, lo_x, lo_y) world position, written by the density pass
     float4* gvel;                 // per step: (v_x, v_y, arm_x, arm_y)
-    unsigned short* nbl;          // per tile [kNbrMax][max own]: staged index of each fluid neighbour
-    unsigned char* nbn;           // per tile [max own]: neighbour count (> kNbrMax: not recorded)
+    unsigned int* nbm;            // per tile [3 stencil rows][max own]: bit k set if staged particle a + k is a fluid neighbour
+    unsigned short* nba;          // per tile [3][max own]: a, the row's first candidate (staged index)
+    unsigned char* nbn;           // per tile [max own]: fluid neighbour count (kNbrNone: rows not recorded)
     unsigned char* srec;          // per tile: the staged order the density pass leaves for the force pass (StageRec)
     // forward-mode tangent (JVP) state, allocated on first use
     float4* tpv[2];               // per slot (dx, dy, dvx, dvy), binned with the primal

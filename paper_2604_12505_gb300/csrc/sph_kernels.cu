@@ -85,10 +85,14 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (TAN) ti = sm.tpv[e];
         // the fluid neighbours found here (staged index, r < 2h, j != i) are
-        // recorded for the force pass, which stages the tile identically
+        // recorded for the force pass, which stages the tile identically: per
+        // stencil row, its first candidate a and a mask of the candidates
+        // a + k that are neighbours (a row of more than kNbrRowBits
+        // candidates is not recorded, and the force pass scans the stencil)
         const bool rec = t < Sh::MAXOWN;
-        unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
+        const size_t rec_at = (size_t)blockIdx.x * (3 * Sh::MAXOWN) + t;
         int nn = 0;
+        bool wide = false;
         const float xlo = pi.x - T.clip, xhi = pi.x + T.clip;
         // each cell is sorted by x: of the row's left cell only the suffix
         // with x >= x_i - clip, of its right cell only the prefix with
@@ -106,6 +110,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             const int cl = c + dy * Sh::SX - 1;
             const int a = lower_x(sm, sm.start[cl], sm.start[cl + 1], xlo);
             const int z = lower_x(sm, sm.start[cl + 2], sm.start[cl + 3], xhi);
+            wide |= z - a > kNbrRowBits;
+            unsigned int bits = 0u, bit = 1u;  // bit = 1 << (j - a); 0 past kNbrRowBits candidates
             for (int j = a; j < z; ++j) {
                 const float4 pj = sm.pv[j];
                 const float2 d = sep_ff(pi, li, pj, sm.plo[j]);
@@ -118,8 +124,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 const float f = fmaf(-4.0f * qb * qb, qb, qa * qa * qa);
                 Sf += in ? f : 0.0f;
                 const bool nb = in && (j != e);
-                if (nb && rec && nn < kNbrMax) lst[nn * Sh::MAXOWN] = (unsigned short)j;
-                nn += nb ? 1 : 0;
+                bits |= nb ? bit : 0u;
+                bit <<= 1;
                 const bool nd = nb && r2 > 0.f;
                 if (want_drho || TAN) {
                     const float gW = T.cdW * fmaf(12.0f * qb, qb, -3.0f * qa * qa) * inv_r;  // (dW/dr) / r
@@ -130,9 +136,14 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                     }
                 }
             }
+            nn += __popc(bits);
+            if (rec) {
+                S.nbm[rec_at + (dy + 1) * Sh::MAXOWN] = bits;
+                S.nba[rec_at + (dy + 1) * Sh::MAXOWN] = (unsigned short)a;
+            }
         }
         Sf *= T.cW;
-        if (rec) S.nbn[blockIdx.x * Sh::MAXOWN + t] = (unsigned char)min(nn, 255);
+        if (rec) S.nbn[blockIdx.x * Sh::MAXOWN + t] = wide ? kNbrNone : (unsigned char)nn;
         float Sg = 0.f, Dg = 0.f;
         int ng2 = 0;
         // one ghost within reach: gp = (x_hi, y_hi, x_lo, y_lo) world position,
@@ -665,13 +676,9 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                     }
                 }
             };
-            const int nn = t < Sh::MAXOWN ? (int)S.nbn[blockIdx.x * Sh::MAXOWN + t] : 255;
-            if (nn <= kNbrMax) {  // the list recorded by the density pass (dense: no candidate tests)
-                const unsigned short* lst = S.nbl + (size_t)blockIdx.x * (kNbrMax * Sh::MAXOWN) + t;
-                nff = nn;
-#pragma unroll 4
-                for (int k = 0; k < nn; ++k) pair(lst[k * Sh::MAXOWN]);
-            } else {              // list overflow: scan the 3x3 cells
+            // the neighbours recorded by the density pass (no candidate tests)
+            if (for_recorded_neighbours<Sh::MAXOWN>(S, blockIdx.x, t, [&](int j) { ++nff; pair(j); })) {
+            } else {              // not recorded: scan the 3x3 cells
 #pragma unroll
                 for (int dy = -1; dy <= 1; ++dy) {
                     const int a = sm.start[c + dy * Sh::SX - 1], zz = sm.start[c + dy * Sh::SX + 2];

@@ -284,6 +284,30 @@ __device__ __forceinline__ int lower_x(const Stg& sm, int lo, int hi, float v)
 }
 
 // Smem index of the t-th own particle (own cells are TY contiguous row runs).
+// The fluid neighbours that the density pass recorded for own particle t of
+// a tile: for each of the three stencil rows, in row order, the staged
+// indices a + k for the set bits k of the row's mask, ascending -- the order
+// in which that pass met them.  Returns false when nothing was recorded
+// (t beyond the record, or a row of more than kNbrRowBits candidates); the
+// caller then scans the stencil.
+template <int MAXOWN, class F>
+__device__ __forceinline__ bool for_recorded_neighbours(const SimDev& S, int tile, int t, F&& pair)
+{
+    if (t >= MAXOWN || S.nbn[(size_t)tile * MAXOWN + t] == kNbrNone) return false;
+    const size_t o = (size_t)tile * (3 * MAXOWN) + t;
+    unsigned int m[3];
+    int a[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        m[r] = S.nbm[o + r * MAXOWN];
+        a[r] = S.nba[o + r * MAXOWN];
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+        for (unsigned int b = m[r]; b; b &= b - 1) pair(a[r] + __ffs(b) - 1);
+    return true;
+}
+
 template <int TX, int TY, bool RHO, bool TAN>
 __device__ __forceinline__ int own_index(int t, const Stage<TX, TY, RHO, TAN>& sm)
 {
