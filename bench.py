@@ -306,6 +306,8 @@ def velocity_surrogate(size: str) -> dict:
         "closed_loop": {"sims": th["surrogate_sims"], "samples": th["samples"], "Ts": r["Ts"],
                         "seconds": val["seconds"], "surrogate_s": th["surrogate_s"], "sph_s": val["sph_device_s"]},
         "fit": {k: {"loss": v["loss"]} for k, v in r["fit"].items() if isinstance(v, dict) and "loss" in v},
+        "lpv_kept": r["fit"]["lpv"]["kept"],
+        "all_channels_within_5pct": {m: max(nrmse[m].values()) <= 0.05 for m in ("lpv", "lti")},
         "wall_s": time.perf_counter() - t0,
     }
 

@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             const int z = lower_x(sm, sm.start[cl + 2], sm.start[cl + 3], xhi);
             wide |= z - a > kNbrRowBits;
             unsigned int bits = 0u, bit = 1u;  // bit = 1 << (j - a); 0 past kNbrRowBits candidates
+#pragma unroll 2
             for (int j = a; j < z; ++j) {
                 const float4 pj = sm.pv[j];
                 const float2 d = sep_ff(pi, li, pj, sm.plo[j]);

@@ -302,9 +302,20 @@ __device__ __forceinline__ bool for_recorded_neighbours(const SimDev& S, int til
         m[r] = S.nbm[o + r * MAXOWN];
         a[r] = S.nba[o + r * MAXOWN];
     }
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-        for (unsigned int b = m[r]; b; b &= b - 1) pair(a[r] + __ffs(b) - 1);
+    // one loop over all recorded neighbours (lanes diverge only by their
+    // totals), moving to the next non-empty row when a row's bits run out
+    const int n = __popc(m[0]) + __popc(m[1]) + __popc(m[2]);
+    unsigned int b = m[0], b1 = m[1], b2 = m[2];
+    int ar = a[0], a1 = a[1], a2 = a[2];
+    for (int k = 0; k < n; ++k) {
+        if (b == 0) {
+            b = b1; ar = a1; b1 = b2; a1 = a2; b2 = 0u;
+            if (b == 0) { b = b1; ar = a1; b1 = 0u; }
+        }
+        const int j = ar + __ffs(b) - 1;
+        b &= b - 1;
+        pair(j);
+    }
     return true;
 }
 
