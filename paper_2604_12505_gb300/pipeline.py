@@ -309,6 +309,42 @@ def surrogate_study(n_tanks: int = 256, launches: int = 4, steps: int = 10_000, 
     return out
 
 
+def size_sweep(dxs=(0.02, 0.005, 0.002, 0.0014, 0.001, 0.0007), relax: int = 3000, steps: int = 1000,
+               log=None) -> list:
+    """Step time against tank size: the R = 0.5 m, 50 % fill tank at each dx
+    (dt = 5e-5 s), relaxed with `relax` damped steps, autotuned, then `steps`
+    graph-replayed steps timed with CUDA events; plus the Tables 1-2
+    spacecraft with three rings.  Reports particles, tile, us per step, pair
+    interactions per step and per second, and the health flags."""
+    from . import workloads as W
+
+    say = log or (lambda *a: None)
+    cases = [(f"R=0.5 m, dx={dx}", dict(W.BASE, dx=dx)) for dx in dxs] + [("Tables 1-2, three rings", dict(W.PAPER_RINGS))]
+    out = []
+    for name, cfg in cases:
+        with Sim(cfg) as sim:
+            sim.relax(relax, damping=2e-3)
+            xv, body = sim.state()
+            xv[:, 2:] = 0.0
+            sim.set_state(xv, body)
+            tile, _ = sim.autotune(steps=32)
+            sim.step(64, record=False)
+            c0 = sim.pair_count()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            sim.step(steps, record=False)
+            e1.record()
+            torch.cuda.synchronize()
+            us = 1e3 * e0.elapsed_time(e1) / steps
+            pairs = (sim.pair_count() - c0) / steps
+            r = dict(tank=name, particles=int(sim.n_fluid[0]), tile=int(tile), us_per_step=us, pairs_per_step=pairs,
+                     pairs_per_s=pairs / (us * 1e-6), flags=sim.check(reset=True, raise_on_error=False))
+        say("size sweep", r)
+        out.append(r)
+    return out
+
+
 def linearization_study(cfg: dict | None = None, relax: int = 2000, steps: int = 2000, n_points: int = 3,
                         tau: float = 5.0, block: int = 1024, log=None) -> dict:
     """Eigenvalues of the linearised dynamics along a manoeuvre (Section 5.2,
@@ -626,9 +662,11 @@ if __name__ == "__main__":
             kw["dx"] = (0.006, 0.006)
         r = surrogate_study(**kw, log=lambda *a: print(*a, file=sys.stderr))
         print(json.dumps(r))
+    elif len(sys.argv) > 1 and sys.argv[1] == "sweep":
+        print(json.dumps(size_sweep(log=lambda *a: print(*a, file=sys.stderr))))
     elif len(sys.argv) > 1 and sys.argv[1] == "velocity":
         print(json.dumps(velocity_surrogate_study(log=lambda *a: print(*a, file=sys.stderr))))
     else:
-        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper [clamp]|surrogate [fill_only]|velocity",
+        print("usage: python -m paper_2604_12505_gb300.pipeline linearize|paper [clamp]|surrogate [fill_only]|sweep|velocity",
               file=sys.stderr)
         sys.exit(2)
