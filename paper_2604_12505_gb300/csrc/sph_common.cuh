@@ -236,8 +236,8 @@ struct SimDev {
     const int* gstart;            // per tank (G*G + 1) ghost-cell starts (global ghost index)
     float4* gpos;                 // per step: (hi_x, hi_y, lo_x, lo_y) world position, written by the density pass
     float4* gvel;                 // per step: (v_x, v_y, arm_x, arm_y)
-    unsigned int* nbm;            // per tile [3 stencil rows][max own]: bit k set if staged particle a + k is a fluid neighbour
-    unsigned short* nba;          // per tile [3][max own]: a, the row's first candidate (staged index)
+    unsigned int* nbm;            // per tile [3 stencil rows][max own]: bit k set if staged particle zl - k is a fluid neighbour
+    unsigned short* nba;          // per tile [3][max own]: zl, the row's last candidate (staged index)
     unsigned char* nbn;           // per tile [max own]: fluid neighbour count (kNbrNone: rows not recorded)
     unsigned char* srec;          // per tile: the staged order the density pass leaves for the force pass (StageRec)
     // forward-mode tangent (JVP) state, allocated on first use

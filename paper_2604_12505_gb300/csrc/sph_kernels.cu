@@ -26,6 +26,7 @@
 
 #include "sph_common.cuh"
 #include "sph_launch.h"
+#include <type_traits>
 #include "sph_tile.cuh"
 
 namespace sph {
@@ -86,8 +87,8 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         if constexpr (TAN) ti = sm.tpv[e];
         // the fluid neighbours found here (staged index, r < 2h, j != i) are
         // recorded for the force pass, which stages the tile identically: per
-        // stencil row, its first candidate a and a mask of the candidates
-        // a + k that are neighbours (a row of more than kNbrRowBits
+        // stencil row, its last candidate zl and a mask of the candidates
+        // zl - k that are neighbours (a row of more than kNbrRowBits
         // candidates is not recorded, and the force pass scans the stencil)
         const bool rec = t < Sh::MAXOWN;
         const size_t rec_at = (size_t)blockIdx.x * (3 * Sh::MAXOWN) + t;
@@ -105,44 +106,51 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         // (W = sigma / h^2 f); r = r^2 rsqrt(max(r^2, FLT_MIN)) is exactly 0
         // for the particle itself, giving W(0) = 4 sigma / h^2.  The tangent
         // variant runs the same arithmetic, so its primal equals the step's.
+        // the candidate loop in two copies, with and without the continuity
+        // sum (an evaluation output), so that the step's copy carries no
+        // branch on it
+        auto rows = [&](auto drho_tag) {
+            constexpr bool want_drho = decltype(drho_tag)::value;
 #pragma unroll
-        for (int dy = -1; dy <= 1; ++dy) {
-            const int cl = c + dy * Sh::SX - 1;
-            const int a = lower_x(sm, sm.start[cl], sm.start[cl + 1], xlo);
-            const int z = lower_x(sm, sm.start[cl + 2], sm.start[cl + 3], xhi);
-            wide |= z - a > kNbrRowBits;
-            unsigned int bits = 0u, bit = 1u;  // bit = 1 << (j - a); 0 past kNbrRowBits candidates
+            for (int dy = -1; dy <= 1; ++dy) {
+                const int cl = c + dy * Sh::SX - 1;
+                const int a = lower_x(sm, sm.start[cl], sm.start[cl + 1], xlo);
+                const int z = lower_x(sm, sm.start[cl + 2], sm.start[cl + 3], xhi);
+                wide |= z - a > kNbrRowBits;
+                unsigned int bits = 0u;  // candidate j at bit z - 1 - j (the row's last candidate at bit 0)
 #pragma unroll 2
-            for (int j = a; j < z; ++j) {
-                const float4 pj = sm.pv[j];
-                const float2 d = sep_ff(pi, li, pj, sm.plo[j]);
-                const float ddx = d.x, ddy = d.y;
-                const float r2 = dist2(ddx, ddy);
-                const bool in = r2 < T.R2;
-                const float inv_r = rsqrtf(fmaxf(r2, FLT_MIN));
-                const float q = r2 * inv_r * T.inv_h;
-                const float qa = 2.0f - q, qb = fmaxf(1.0f - q, 0.0f);
-                const float f = fmaf(-4.0f * qb * qb, qb, qa * qa * qa);
-                Sf += in ? f : 0.0f;
-                const bool nb = in && (j != e);
-                bits |= nb ? bit : 0u;
-                bit <<= 1;
-                const bool nd = nb && r2 > 0.f;
-                if (want_drho || TAN) {
-                    const float gW = T.cdW * fmaf(12.0f * qb, qb, -3.0f * qa * qa) * inv_r;  // (dW/dr) / r
-                    if (want_drho) Df += nd ? ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * gW : 0.0f;
-                    if constexpr (TAN) {
-                        const float4 tj = sm.tpv[j];
-                        dRf += nd ? (ddx * (ti.x - tj.x) + ddy * (ti.y - tj.y)) * gW : 0.0f;
+                for (int j = a; j < z; ++j) {
+                    const float4 pj = sm.pv[j];
+                    const float2 d = sep_ff(pi, li, pj, sm.plo[j]);
+                    const float ddx = d.x, ddy = d.y;
+                    const float r2 = dist2(ddx, ddy);
+                    const bool in = r2 < T.R2;
+                    const float inv_r = rsqrtf(fmaxf(r2, FLT_MIN));
+                    const float q = r2 * inv_r * T.inv_h;
+                    const float qa = 2.0f - q, qb = fmaxf(1.0f - q, 0.0f);
+                    const float f = fmaf(-4.0f * qb * qb, qb, qa * qa * qa);
+                    Sf += in ? f : 0.0f;
+                    const bool nb = in && (dy != 0 || j != e);  // the particle itself lies in its own row
+                    bits = 2u * bits + (nb ? 1u : 0u);
+                    const bool nd = nb && r2 > 0.f;
+                    if (want_drho || TAN) {
+                        const float gW = T.cdW * fmaf(12.0f * qb, qb, -3.0f * qa * qa) * inv_r;  // (dW/dr) / r
+                        if (want_drho) Df += nd ? ((pi.z - pj.z) * ddx + (pi.w - pj.w) * ddy) * gW : 0.0f;
+                        if constexpr (TAN) {
+                            const float4 tj = sm.tpv[j];
+                            dRf += nd ? (ddx * (ti.x - tj.x) + ddy * (ti.y - tj.y)) * gW : 0.0f;
+                        }
                     }
                 }
+                nn += __popc(bits);
+                if (rec) {
+                    S.nbm[rec_at + (dy + 1) * Sh::MAXOWN] = bits;
+                    S.nba[rec_at + (dy + 1) * Sh::MAXOWN] = (unsigned short)(z - 1);
+                }
             }
-            nn += __popc(bits);
-            if (rec) {
-                S.nbm[rec_at + (dy + 1) * Sh::MAXOWN] = bits;
-                S.nba[rec_at + (dy + 1) * Sh::MAXOWN] = (unsigned short)a;
-            }
-        }
+        };
+        if (want_drho) rows(std::integral_constant<bool, true>{});
+        else rows(std::integral_constant<bool, false>{});
         Sf *= T.cW;
         if (rec) S.nbn[blockIdx.x * Sh::MAXOWN + t] = wide ? kNbrNone : (unsigned char)nn;
         float Sg = 0.f, Dg = 0.f;

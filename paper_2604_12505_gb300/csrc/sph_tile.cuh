@@ -286,8 +286,8 @@ __device__ __forceinline__ int lower_x(const Stg& sm, int lo, int hi, float v)
 // Smem index of the t-th own particle (own cells are TY contiguous row runs).
 // The fluid neighbours that the density pass recorded for own particle t of
 // a tile: for each of the three stencil rows, in row order, the staged
-// indices a + k for the set bits k of the row's mask, ascending -- the order
-// in which that pass met them.  Returns false when nothing was recorded
+// indices zl - k for the set bits k of the row's mask (zl the row's last
+// candidate), highest bit first -- the order in which that pass met them.  Returns false when nothing was recorded
 // (t beyond the record, or a row of more than kNbrRowBits candidates); the
 // caller then scans the stencil.
 template <int MAXOWN, class F>
@@ -312,8 +312,9 @@ __device__ __forceinline__ bool for_recorded_neighbours(const SimDev& S, int til
             b = b1; ar = a1; b1 = b2; a1 = a2; b2 = 0u;
             if (b == 0) { b = b1; ar = a1; b1 = 0u; }
         }
-        const int j = ar + __ffs(b) - 1;
-        b &= b - 1;
+        const int lz = __clz(b);  // the highest set bit: the earliest candidate left
+        const int j = ar - 31 + lz;
+        b &= 0x7fffffffu >> lz;
         pair(j);
     }
     return true;
