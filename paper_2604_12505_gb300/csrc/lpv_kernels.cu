@@ -27,6 +27,8 @@
 
 namespace lpv {
 
+constexpr int kPrefetch = 4;  // steps of inputs in flight in the recurrences
+
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, uint32_t b0, uint32_t b1)
 {
     asm volatile(
@@ -143,7 +145,7 @@ __device__ __forceinline__ void load_step(const Dims& d, const float* __restrict
 // prediction (physical units); MODE 1 accumulates the squared error of the
 // normalised outputs and records, per step, x_k and dJ/dy_k for the
 // backward pass in hist[traj][k][16] (state columns, then output columns).
-// The inputs of step k + 1 are loaded while step k's products run.
+// The inputs of steps k + 1 .. k + kPrefetch are in flight while step k's products run.
 template <int MODE>
 __global__ void __launch_bounds__(128) fwd_kernel(const float* __restrict__ Wp, Dims d, const float* __restrict__ u,
                                                   const float* __restrict__ p, const float* __restrict__ y, int n_traj,
@@ -158,11 +160,20 @@ __global__ void __launch_bounds__(128) fwd_kernel(const float* __restrict__ Wp, 
     load_fwd_frags(Wp, bhi, blo, d.nkt, g, t);
     float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // x_0 = 0
     float lsum_f = 0.f;                     // widened to FP64 once, after the loop
-    StepIn cur;
-    load_step<MODE == 1>(d, u, p, y, r0, r1, v0, v1, T, 0, t, cur);
-    for (int k = 0; k < T; ++k) {
-        StepIn nxt;
-        load_step<MODE == 1>(d, u, p, y, r0, r1, v0, v1, T, k + 1 < T ? k + 1 : k, t, nxt);
+    // a ring of the inputs of the next kPrefetch steps: the loads of step
+    // k + kPrefetch are issued when step k starts, so a step waits on no
+    // global load issued less than kPrefetch steps before it
+    StepIn ring[kPrefetch];
+#pragma unroll
+    for (int i = 0; i < kPrefetch; ++i)
+        load_step<MODE == 1>(d, u, p, y, r0, r1, v0, v1, T, i < T ? i : T - 1, t, ring[i]);
+    for (int k0 = 0; k0 < T; k0 += kPrefetch) {
+#pragma unroll
+    for (int i = 0; i < kPrefetch; ++i) {
+        const int k = k0 + i;
+        if (k >= T) break;
+        const StepIn cur = ring[i];
+        load_step<MODE == 1>(d, u, p, y, r0, r1, v0, v1, T, k + kPrefetch < T ? k + kPrefetch : T - 1, t, ring[i]);
         float z[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) z[i] = (scol(i, t) < d.nx) ? s[i] : cur.uz[i];
@@ -196,7 +207,7 @@ __global__ void __launch_bounds__(128) fwd_kernel(const float* __restrict__ Wp, 
             }
             s[i] = (c < d.nx) ? D[i] : 0.f;
         }
-        cur = nxt;
+    }
     }
     if (MODE == 1) {
         double lsum = (double)lsum_f;
@@ -249,8 +260,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) bwd_kernel(const float* __rest
     float gacc[6][4];
 #pragma unroll
     for (int nt = 0; nt < 6; ++nt) gacc[nt][0] = gacc[nt][1] = gacc[nt][2] = gacc[nt][3] = 0.f;
-    // step inputs: scheduling, recorded history (x_k | dJ/dy_k) and u; those of
-    // step k - 1 are loaded while step k's products run
+    // step inputs: scheduling, recorded history (x_k | dJ/dy_k) and u
     auto fetch = [&](int k, float* pa0, float* pa1, float* hv, float* uz) {
         load_p(d, p, r0, v0, T, k, pa0);
         load_p(d, p, r1, v1, T, k, pa1);
@@ -264,12 +274,25 @@ __global__ void __launch_bounds__(32 * kBwdWarps) bwd_kernel(const float* __rest
                         ? u[((size_t)r * T + k) * d.nu + (c - d.nx)] * d.inv_su[c - d.nx] : 0.f;
         }
     };
-    float cp0[2], cp1[2], chv[8], cuz[8];
-    fetch(T - 1, cp0, cp1, chv, cuz);
-    for (int k = T - 1; k >= 0; --k) {
-        float np0[2], np1[2], nhv[8], nuz[8];
-        fetch(k > 0 ? k - 1 : 0, np0, np1, nhv, nuz);
-        float G[8], z[8], pp0[2] = {cp0[0], cp0[1]}, pp1[2] = {cp1[0], cp1[1]};
+    // a ring of the inputs of the next kPrefetch steps (backwards in k), as in
+    // the forward pass
+    float rp0[kPrefetch][2], rp1[kPrefetch][2], rhv[kPrefetch][8], ruz[kPrefetch][8];
+#pragma unroll
+    for (int i = 0; i < kPrefetch; ++i) fetch(T - 1 - i >= 0 ? T - 1 - i : 0, rp0[i], rp1[i], rhv[i], ruz[i]);
+    for (int k0 = T - 1; k0 >= 0; k0 -= kPrefetch) {
+#pragma unroll
+    for (int ri = 0; ri < kPrefetch; ++ri) {
+        const int k = k0 - ri;
+        if (k < 0) break;
+        float chv[8], cuz[8];
+        const float pp0[2] = {rp0[ri][0], rp0[ri][1]}, pp1[2] = {rp1[ri][0], rp1[ri][1]};
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            chv[i] = rhv[ri][i];
+            cuz[i] = ruz[ri][i];
+        }
+        fetch(k - kPrefetch >= 0 ? k - kPrefetch : 0, rp0[ri], rp1[ri], rhv[ri], ruz[ri]);
+        float G[8], z[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const int c = scol(i, t);
@@ -327,15 +350,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) bwd_kernel(const float* __rest
             mma16816(gacc[nt], alo, b0h, b1h);
         }
         __syncwarp();
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            chv[i] = nhv[i];
-            cuz[i] = nuz[i];
-        }
-        cp0[0] = np0[0];
-        cp0[1] = np0[1];
-        cp1[0] = np1[0];
-        cp1[1] = np1[1];
+    }
     }
     // gacc[nt]: (o = g, f = 8 nt + 2t), (g, +1), (g + 8, 2t), (g + 8, 2t + 1)
     float* out = gpart + (size_t)wid * kWN;
@@ -373,7 +388,7 @@ struct BodyPar {
 // thetadot], and n_sub kick-then-drift substeps of the body under the held
 // forces, summed in closed form: v += n dt a, x += n dt v + dt^2 a n(n+1)/2.
 // The body state (FP32) is replicated in the four lanes of each row group.
-__global__ void __launch_bounds__(128) closed_loop_kernel(const float* __restrict__ Wp, Dims d, int B, int T,
+__global__ void __launch_bounds__(128, 4) closed_loop_kernel(const float* __restrict__ Wp, Dims d, int B, int T,
                                                           const double* __restrict__ F, const double* __restrict__ tau,
                                                           const double* __restrict__ ref,
                                                           const double* __restrict__ fill, BodyPar bp,
