@@ -347,6 +347,7 @@ __global__ void set_step_kernel(RunDev* run, long long step)
     run->step = step;
     run->step0 = step;
     run->tanks_done = 0;
+    run->next_buf = (int)(step & 1);
 }
 
 cudaError_t launch_set_step(RunDev* run, long long step, cudaStream_t st)

@@ -190,9 +190,11 @@ struct sph_sim {
         return s;
     }
 
-    int step_launch(const EvalOut& E, int eval, cudaStream_t st)
+    // chained: the previous launch on st was a step of the same sequence
+    int step_launch(const EvalOut& E, int eval, cudaStream_t st, bool chained = false)
     {
-        cudaError_t e = launch_step(dev(), E, eval, tile_code, n_tiles[tile_code], st, use_pdl && !eval);
+        cudaError_t e = launch_step(dev(), E, eval, tile_code, n_tiles[tile_code], st, use_pdl && !eval, false,
+                                    chained && !eval);
         if (e != cudaSuccess) return fail(SPH_E_CUDA, std::string("step launch: ") + cudaGetErrorString(e));
         return SPH_OK;
     }
@@ -523,7 +525,7 @@ int ensure_graph(sph_sim* s)
     CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeThreadLocal));
     EvalOut E{};
     for (int i = 0; i < kGraphSteps; ++i) {
-        int rc = s->step_launch(E, 0, s->cap);
+        int rc = s->step_launch(E, 0, s->cap, i > 0);
         if (rc) {
             cudaStreamEndCapture(s->cap, &g);
             if (g) cudaGraphDestroy(g);
@@ -657,8 +659,8 @@ int sph_step(sph_sim* sim, const double* u, int32_t n_steps, const sph_ctrl* pd,
         CK(cudaGraphLaunch(sim->graph, st));
         left -= kGraphSteps;
     }
-    for (; left > 0; --left) {
-        rc = sim->step_launch(E, 0, st);
+    for (int i = 0; left > 0; --left, ++i) {
+        rc = sim->step_launch(E, 0, st, i > 0);
         if (rc) return rc;
     }
     sim->host_step += n_steps;
@@ -675,7 +677,7 @@ int sph_relax(sph_sim* sim, int32_t n_steps, double damping, void* stream)
     CK(launch_set_run(sim->d_run, d, st));
     EvalOut E{};
     for (int i = 0; i < n_steps; ++i) {
-        int rc = sim->step_launch(E, 0, st);
+        int rc = sim->step_launch(E, 0, st, i > 0);
         if (rc) return rc;
     }
     sim->host_step += n_steps;

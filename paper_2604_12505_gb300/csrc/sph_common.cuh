@@ -171,6 +171,7 @@ struct RunDev {
     const double* du;             // tangent of the input, [B, n_rows, 3] (NULL: 0)
     double* dy;                   // tangent samples [B, n_samples, SPH_NY] (NULL: none)
     unsigned int tanks_done;      // tanks finished in the current force pass
+    int next_buf;                 // buffer of the next step's state, written by the force pass (step & 1)
 };
 
 // A two-float (hi + lo) compensated sum: error-free transformations keep

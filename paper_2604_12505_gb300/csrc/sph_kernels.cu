@@ -38,7 +38,7 @@ namespace sph {
 // tangent of positions and of the body pose) and d(P / rho^2).
 template <int TX, int TY, bool TAN>
 __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY>::DENSITY_MIN_CTAS)
-    density_kernel(SimDev S, EvalOut E, int eval)
+    density_kernel(SimDev S, EvalOut E, int eval, int chained)
 {
     using Sh = Shape<TX, TY>;
     __shared__ Stage<TX, TY, false, TAN> sm;
@@ -46,8 +46,20 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     const int4 td = S.tiles[blockIdx.x];
     const TankDev T = S.tank[td.x];  // by value: the constants live in registers
     const int cx0 = td.y, cy0 = td.z;
-    pdl_wait();
-    const int buf = (int)(S.run->step & 1), nbuf = buf ^ 1;
+    // chained (a step after a step of the same sequence): the staging and the
+    // fluid part of Eq. 14 read only what the previous force pass wrote, and
+    // that pass completed before the body update passed its dependency, so
+    // they run before this pass's dependency on the body update (through L2:
+    // the staging loads bypass L1); the ghosts wait for the body
+    const bool early = !TAN && chained;
+    int buf;
+    if (early) {
+        buf = __ldcg(&S.run->next_buf);
+    } else {
+        pdl_wait();
+        buf = (int)(S.run->step & 1);
+    }
+    const int nbuf = buf ^ 1;
 
     // clear the other buffer's counts of the own cells (it is re-filled by the force pass)
     for (int c = threadIdx.x; c < TX * TY; c += blockDim.x) {
@@ -60,29 +72,18 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     const int n_own = sm.own_row[TY];
     if (n_own == 0) return;
 
-    const BodyDev& b = S.body[td.x];
-    int gmode = kGhostsGlobal;  // the tangent variant visits the ghosts through global memory
-    if constexpr (!TAN) gmode = stage_ghosts<true>(S, T, b, sm, n_own, gs);
-    const float bc = b.fc, bs = b.fs, brx = b.frx, bry = b.fry;
-    const GhostFrame fr = ghost_frame(b);
-    const float fw = fr.fw;
     const bool want_drho = eval && E.drho;
-    float t_rx = 0.f, t_ry = 0.f, t_th = 0.f, t_vx = 0.f, t_vy = 0.f, t_w = 0.f;
-    if constexpr (TAN) {
-        t_rx = b.ftr[0];
-        t_ry = b.ftr[1];
-        t_th = b.ftth;
-        t_vx = b.ftv[0];
-        t_vy = b.ftv[1];
-        t_w = b.ftw;
-    }
-
-    for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
+    // the fluid part of own particle t: Sf (Eq. 14's fluid sum), Df (the
+    // fluid part of the continuity sum, evaluation only) and, in the tangent
+    // variant, dRf; the neighbour record for the force pass
+    auto fluid_part = [&](int t, float& Sf, float& Df, float& dRf) {
         const int e = own_index(t, sm);
         const float4 pi = sm.pv[e];
         const float2 li = sm.plo[e];
         const int c = sm.cell[e];
-        float Sf = 0.f, Df = 0.f, dRf = 0.f, dRg = 0.f;
+        Sf = 0.f;
+        Df = 0.f;
+        dRf = 0.f;
         float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
         if constexpr (TAN) ti = sm.tpv[e];
         // the fluid neighbours found here (staged index, r < 2h, j != i) are
@@ -151,8 +152,40 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
         };
         if (want_drho) rows(std::integral_constant<bool, true>{});
         else rows(std::integral_constant<bool, false>{});
-        Sf *= T.cW;
+        Sf = __fmul_rn(Sf, T.cW);  // rounded here in every variant (no contraction with the ghost sum)
         if (rec) S.nbn[blockIdx.x * Sh::MAXOWN + t] = wide ? kNbrNone : (unsigned char)nn;
+    };
+
+    // after the body update: the ghosts of Eqs. 14 and 21, then rho and P
+    const BodyDev& b = S.body[td.x];
+    int gmode = kGhostsGlobal;  // the tangent variant visits the ghosts through global memory
+    float bc = 0.f, bs = 0.f, brx = 0.f, bry = 0.f, fw = 0.f;
+    GhostFrame fr{};
+    float t_rx = 0.f, t_ry = 0.f, t_th = 0.f, t_vx = 0.f, t_vy = 0.f, t_w = 0.f;
+    auto body_frame = [&]() {
+        if constexpr (!TAN) gmode = stage_ghosts<true>(S, T, b, sm, n_own, gs);
+        bc = b.fc;
+        bs = b.fs;
+        brx = b.frx;
+        bry = b.fry;
+        fr = ghost_frame(b);
+        fw = fr.fw;
+        if constexpr (TAN) {
+            t_rx = b.ftr[0];
+            t_ry = b.ftr[1];
+            t_th = b.ftth;
+            t_vx = b.ftv[0];
+            t_vy = b.ftv[1];
+            t_w = b.ftw;
+        }
+    };
+    auto ghost_part = [&](int t, float Sf, float Df, float dRf) {
+        const int e = own_index(t, sm);
+        const float4 pi = sm.pv[e];
+        const float2 li = sm.plo[e];
+        float dRg = 0.f;
+        float4 ti = make_float4(0.f, 0.f, 0.f, 0.f);
+        if constexpr (TAN) ti = sm.tpv[e];
         float Sg = 0.f, Dg = 0.f;
         int ng2 = 0;
         // one ghost within reach: gp = (x_hi, y_hi, x_lo, y_lo) world position,
@@ -195,9 +228,11 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
                 ghost(gp, gv, tgx, tgy);
             });
         }
-        const float rho = T.m * (Sf + T.gamma1 * Sg);          // Eq. 14
-        const float P = T.k * (rho - T.rho0);                  // Eq. 11
-        const float pr2 = P / (rho * rho);
+        // explicit roundings, so that the variants (fluid sums through shared
+        // memory or in registers) take the same arithmetic
+        const float rho = __fmul_rn(T.m, __fmaf_rn(T.gamma1, Sg, Sf));       // Eq. 14
+        const float P = __fmul_rn(T.k, __fsub_rn(rho, T.rho0));               // Eq. 11
+        const float pr2 = __fdiv_rn(P, __fmul_rn(rho, rho));
         S.rhoP[sm.slot[e]] = make_float2(rho, pr2);
         if constexpr (TAN) {  // d rho, and d(P/rho^2) = d rho (k / rho^2 - 2 P / rho^3)
             const float trh = T.m * (dRf + T.gamma1 * dRg);
@@ -209,6 +244,28 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
             if (E.drho) E.drho[id] = T.m * (Df + T.gamma1 * Dg);
             if (E.nbr) E.nbr[3 * id + 1] = ng2;
         }
+    };
+
+    if constexpr (TAN) {
+        body_frame();
+        for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
+            float Sf, Df, dRf;
+            fluid_part(t, Sf, Df, dRf);
+            ghost_part(t, Sf, Df, dRf);
+        }
+    } else {
+        // the fluid sums wait in the staging scratch (key_in, pid_in: free
+        // once the tile is staged), each read back by the thread that wrote it
+        for (int t = threadIdx.x; t < n_own; t += blockDim.x) {
+            float Sf, Df, dRf;
+            fluid_part(t, Sf, Df, dRf);
+            sm.key_in[t] = __float_as_uint(Sf);
+            sm.pid_in[t] = __float_as_int(Df);
+        }
+        if (early) pdl_wait();
+        body_frame();
+        for (int t = threadIdx.x; t < n_own; t += blockDim.x)
+            ghost_part(t, __uint_as_float(sm.key_in[t]), __int_as_float(sm.pid_in[t]), 0.f);
     }
     // the successor's CTAs may be placed once every CTA of this pass is past
     // its particle loop (or has exited): placed earlier, they would wait in
@@ -618,6 +675,9 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     pdl_wait();
     const long long step = S.run->step;
     const int buf = (int)(step & 1), nbuf = buf ^ 1;
+    // the buffer the next density pass stages from, readable before its grid
+    // dependency once this pass has completed
+    if (!eval && blockIdx.x == 0 && threadIdx.x == 0) S.run->next_buf = nbuf;
     const bool sample = !eval && (step % T.outer_every) == 0;
     const float damp = 1.0f - S.run->damping;
 
@@ -1254,6 +1314,7 @@ __global__ void set_run_kernel(RunDev* run, RunDev desc)
     desc.step = run->step;
     desc.step0 = run->step;
     desc.tanks_done = 0;
+    desc.next_buf = (int)(run->step & 1);
     *run = desc;
 }
 
@@ -1278,19 +1339,20 @@ static cudaError_t launch(void (*k)(KArgs...), int grid, int block, cudaStream_t
 
 template <int TX, int TY>
 static cudaError_t launch_tile_phase(const SimDev& S, const EvalOut& E, int eval, int n_tiles, int phase,
-                                     cudaStream_t st, bool pdl, bool tan)
+                                     cudaStream_t st, bool pdl, bool tan, bool chained)
 {
     using Sh = Shape<TX, TY>;
     if (tan) {
         if constexpr (TX * TY <= 32) {  // the tangent staging of 8x8 tiles exceeds static shared memory
-            if (phase == 0) return launch(density_kernel<TX, TY, true>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+            if (phase == 0) return launch(density_kernel<TX, TY, true>, n_tiles, Sh::THREADS, st, pdl, S, E, eval, 0);
             if (phase == 2) return cudaSuccess;  // the tangent force pass updates the body itself
             return launch(force_kernel<TX, TY, true>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
         } else {
             return cudaErrorInvalidValue;
         }
     }
-    if (phase == 0) return launch(density_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
+    if (phase == 0)
+        return launch(density_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval, (pdl && chained) ? 1 : 0);
     if (phase == 1) return launch(force_kernel<TX, TY, false>, n_tiles, Sh::THREADS, st, pdl, S, E, eval);
     return launch(body_kernel, (S.B + kBodyWarps - 1) / kBodyWarps, 32 * kBodyWarps, st, pdl, S, E, eval);
 }
@@ -1319,23 +1381,23 @@ void tile_dims(int code, int* tx, int* ty)
 
 // phase 0: density pass, 1: force pass, 2: body update (none in the tangent variant)
 cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, int phase,
-                         cudaStream_t st, bool pdl, bool tan)
+                         cudaStream_t st, bool pdl, bool tan, bool chained)
 {
     switch (tile_code) {
-    case 1: return launch_tile_phase<2, 2>(S, E, eval, n_tiles, phase, st, pdl, tan);
-    case 2: return launch_tile_phase<4, 2>(S, E, eval, n_tiles, phase, st, pdl, tan);
-    case 3: return launch_tile_phase<4, 4>(S, E, eval, n_tiles, phase, st, pdl, tan);
-    case 4: return launch_tile_phase<8, 4>(S, E, eval, n_tiles, phase, st, pdl, tan);
-    case 5: return launch_tile_phase<8, 8>(S, E, eval, n_tiles, phase, st, pdl, tan);
+    case 1: return launch_tile_phase<2, 2>(S, E, eval, n_tiles, phase, st, pdl, tan, chained);
+    case 2: return launch_tile_phase<4, 2>(S, E, eval, n_tiles, phase, st, pdl, tan, chained);
+    case 3: return launch_tile_phase<4, 4>(S, E, eval, n_tiles, phase, st, pdl, tan, chained);
+    case 4: return launch_tile_phase<8, 4>(S, E, eval, n_tiles, phase, st, pdl, tan, chained);
+    case 5: return launch_tile_phase<8, 8>(S, E, eval, n_tiles, phase, st, pdl, tan, chained);
     default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, cudaStream_t st,
-                        bool pdl, bool tan)
+                        bool pdl, bool tan, bool chained)
 {
     for (int ph = 0; ph < 3; ++ph) {
-        cudaError_t e = launch_phase(S, E, eval, tile_code, n_tiles, ph, st, pdl, tan);
+        cudaError_t e = launch_phase(S, E, eval, tile_code, n_tiles, ph, st, pdl, tan, chained);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;

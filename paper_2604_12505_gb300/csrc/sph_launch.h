@@ -15,10 +15,16 @@ size_t stage_record_bytes(const int* n_tiles);
 // tan: the forward-mode tangent variants (tile codes 1..4 only).
 // Phases: 0 density pass, 1 force pass, 2 body update (the tangent variant's
 // force pass updates the body itself, its phase 2 launches nothing).
+// chained: this step directly follows a step of the same launch sequence
+// (its density pass is the programmatic dependent of the previous step's
+// body update), so that pass may stage the tile and sum the fluid part of
+// Eq. 14 before its grid dependency: everything it reads there was written
+// by the previous force pass, which completed before the body update passed
+// its own dependency.
 cudaError_t launch_phase(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, int phase,
-                         cudaStream_t st, bool pdl, bool tan = false);
+                         cudaStream_t st, bool pdl, bool tan = false, bool chained = false);
 cudaError_t launch_step(const SimDev& S, const EvalOut& E, int eval, int tile_code, int n_tiles, cudaStream_t st,
-                        bool pdl, bool tan = false);
+                        bool pdl, bool tan = false, bool chained = false);
 // State transfer: xv [N, 4] the hi parts of the particle state, lo [N, 4] its
 // low parts (NULL: zero on binning, not read back on gathering).
 cudaError_t launch_bin_flat(const SimDev& S, const float* xv, const float* lo, const int* part_tank, int n, int buf,

@@ -69,7 +69,9 @@ __device__ __forceinline__ unsigned int order_key(float x)
 // (TY+2) staged cells, each cell ordered by x with the particle index
 // breaking ties (a deterministic order, whatever order the slots were
 // claimed in).  Returns false (uniformly over the block) if the staged set
-// does not fit.
+// does not fit.  The counts and the state are read through L2 (ld.global.cg):
+// the density pass may stage before its grid dependency, from data that an
+// earlier, completed grid wrote.
 template <int TX, int TY, bool RHO, bool TAN>
 __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, int cy0, Stage<TX, TY, RHO, TAN>& sm)
 {
@@ -79,7 +81,7 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
     for (int c = tid; c < Sh::NC; c += blockDim.x) {
         int ix = cx0 - 1 + c % Sh::SX, iy = cy0 - 1 + c / Sh::SX;
         int n = 0;
-        if (ix >= 0 && ix < T.G && iy >= 0 && iy < T.G) n = min(max(count[T.cell_base + iy * T.G + ix], 0), kCap);
+        if (ix >= 0 && ix < T.G && iy >= 0 && iy < T.G) n = min(max(__ldcg(count + T.cell_base + iy * T.G + ix), 0), kCap);
         sm.start[c] = n;
     }
     __syncthreads();
@@ -136,8 +138,8 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
         const int ix = cx0 - 1 + lo % Sh::SX, iy = cy0 - 1 + lo / Sh::SX;
         sm.cell[e] = (unsigned char)lo;
         const int gs = (T.cell_base + iy * T.G + ix) * kCap + (e - sm.start[lo]);
-        sm.pid_in[e] = S.pid[buf][gs];
-        sm.key_in[e] = order_key(S.pv[buf][gs].x);
+        sm.pid_in[e] = __ldcg(S.pid[buf] + gs);
+        sm.key_in[e] = order_key(__ldcg(&S.pv[buf][gs].x));
     }
     __syncthreads();
     // pass 2: rank by (x, particle index) inside the cell and gather into
@@ -157,8 +159,8 @@ __device__ bool stage_tile(const SimDev& S, const TankDev& T, int buf, int cx0, 
         const int d = a + rank;
         const int ix = cx0 - 1 + c % Sh::SX, iy = cy0 - 1 + c / Sh::SX;
         const int gs = (T.cell_base + iy * T.G + ix) * kCap + (e - a);
-        sm.pv[d] = S.pv[buf][gs];
-        const float4 lo = S.lo[buf][gs];
+        sm.pv[d] = __ldcg(S.pv[buf] + gs);
+        const float4 lo = __ldcg(S.lo[buf] + gs);
         sm.plo[d] = make_float2(lo.x, lo.y);
         if (RHO) {
             sm.rho[d] = S.rhoP[gs];
