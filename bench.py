@@ -170,7 +170,7 @@ FP32_LANES = 152 * 128
 # code, mean of three launches captured warm (ncu --cache-control none): the
 # working set stays in L2.  Valid for the kernel source they were captured
 # on; a kernel or tile without a capture of the current source reports null.
-TRAFFIC_BYTES: dict[tuple[str, int], int] = {("density", 4): 18_944, ("force", 4): 10_581}
+TRAFFIC_BYTES: dict[tuple[str, int], int] = {("density", 4): 22_613, ("force", 4): 9_387}
 
 
 # --------------------------------------------------------------------------
