@@ -338,7 +338,7 @@ def neighbor_counts_f32(p: Params, xy_f32, gB, body, query=None):
 
 
 def cell_keys_f64(p: Params, xy_f32, anchor):
-    """Cell keys of SURVEY C13's FP64 definition: floor((x - (anchor - W)) / s)
+    """Cell keys by their exact definition: floor((x - (anchor - W)) / s)
     in FP64 on the FP32 positions, clamped to the grid; also returns, per
     particle, whether a coordinate lies within 2^-20 s of a cell boundary
     (where the FP32 convention may take the other cell)."""
@@ -351,8 +351,8 @@ def cell_keys_f64(p: Params, xy_f32, anchor):
 
 
 def neighbor_counts_f64(p: Params, xy_f32, gB, body, query=None, band=2.0 ** -20):
-    """Neighbour counts with the FP64 predicate on the FP32 positions
-    (SURVEY C13): returns (n_ff, n_fg2, n_fg1) and their band counts (pairs
+    """Neighbour counts with the exact predicate, r^2 < (2h)^2 in FP64 on the
+    FP32 positions: returns (n_ff, n_fg2, n_fg1) and their band counts (pairs
     with |r^2 - s^2| <= band s^2), each an int array over ``query``."""
     xy = np.ascontiguousarray(xy_f32, dtype=np.float32)
     gB = np.ascontiguousarray(gB, dtype=np.float64).reshape(-1, 2)

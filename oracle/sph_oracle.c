@@ -809,7 +809,7 @@ int orc_neighbor_counts_f64(const orc_params* p, int nf, const float* xy, int st
  *   out[i][3]  #{ g : r_ig < h, v_ig . r_ig < 0 } (the min(., 0) of Eq. 18)
  * Two states whose counts agree for every particle take every switch the
  * same way, so the step map is smooth between them; where they differ, a
- * pair crossed a support or the viscosity clip.
+ * pair crossed a support or the viscosity clip between them.
  */
 int orc_switch_counts(const orc_params* p, int nf, const double* x, const double* v, int ng, const double* gB,
                       const double* body, int32_t* out)

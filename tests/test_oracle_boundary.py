@@ -82,7 +82,7 @@ def test_gamma1_falls_as_ghost_rows_are_added(orc):
 
 @pytest.mark.parametrize("sign", [-1.0, 1.0])
 def test_ghost_pressure_clamp_reading(orc, sign):
-    # Reading R34: with ghost_pressure_clamp = 1 Eq. 16 takes max(P_i, 0).  A
+    # With ghost_pressure_clamp = 1 Eq. 16 takes max(P_i, 0).  A
     # lone particle next to one ghost has rho_i = m (W(0) + gamma1 W(r)), far
     # below rho0, so P_i < 0: as printed (clamp 0) the wall term pulls it
     # towards the ghost for the repulsive sign (-1); clamped, the wall exerts

@@ -61,7 +61,7 @@ def test_pair_count_equals_fp32_counts_away_from_the_support(orc):
 
 
 def test_fp64_predicate_counts_equal_brute_force(orc):
-    # SURVEY C13's definition: r^2 < (2h)^2 (r^2 < h^2 for Eqs. 16-18) in FP64
+    # The exact predicate: r^2 < (2h)^2 (r^2 < h^2 for Eqs. 16-18) in FP64
     # on the FP32 positions, against an independent NumPy brute force.
     p = orc.params(**W.TINY)
     x, gB = orc.tank(p)

@@ -211,7 +211,7 @@ def test_eos_unclamped(orc):
 
 
 def test_continuity_sum_is_time_derivative_of_density(orc):
-    # Reading R10: the continuity sum equals d rho_i / dt along the kinematic
+    # The continuity sum is read as d rho_i / dt of Eq. 14 along the kinematic
     # motion of fluid (x + t v) and body (pose + t velocity).
     p = orc.params(**W.TINY)
     x, gB = orc.tank(p)

@@ -1,6 +1,9 @@
 """Host-side pieces of the self-scheduled surrogate front end (no GPU): the
 parameter layout agrees with the oracle's, and the starting points of a fit
-have the structure Section 5.3.2 and the design notes state."""
+have the structure of Section 5.3.2: a random LTI start (A_0 = 0.9 I, M_1
+and the network at zero), and restarts that keep M_0, draw M_1's B and C
+blocks (its A and D blocks zero) and Xavier network weights with zero
+biases."""
 import numpy as np
 import pytest
 
