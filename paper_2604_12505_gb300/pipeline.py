@@ -522,7 +522,7 @@ def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int 
                              lti_iters: int = 1000, lti_lr: float = 1e-3, adam_iters: int = 0, lr: float = 1e-4,
                              lbfgs_iters: int = 1000, m1_std: float = 0.0, restarts: int = 8, cl_samples: int = 600,
                              n_sims: int = 65_536,
-                             nx: int = 4,
+                             nx: int = 4, net_scale: float = 1.0,
                              sigma2: float = 1e-4, seed: int = 0, log=None) -> dict:
     """The paper's identification study (Section 5.3) on its spacecraft.
 
@@ -580,7 +580,7 @@ def velocity_surrogate_study(n_train: int = 24, n_val: int = 8, id_samples: int 
     best = (fits["lti"]["loss"], th_lti, -1)
     for r in range(restarts):
         t2 = time.perf_counter()
-        m.set_params(initial_theta(nx, seed=seed * 100 + r + 1, base=th_lti, m1_std=m1_std), sc)
+        m.set_params(initial_theta(nx, seed=seed * 100 + r + 1, base=th_lti, m1_std=m1_std, net_scale=net_scale), sc)
         l0 = float(m.loss_grad(u, y, grad=False)[0].item())
         # Adam on the scheduling part (M_0 held at the LTI fit), then L-BFGS on everything
         if adam_iters > 0:

@@ -150,13 +150,14 @@ def layout(nx: int) -> dict:
 
 
 def initial_theta(nx: int, seed: int, base=None, m1_std: float = 1e-2, a0: float = 0.9,
-                  bc_std: float = 0.1) -> np.ndarray:
+                  bc_std: float = 0.1, net_scale: float = 1.0) -> np.ndarray:
     """Starting point of a fit (Section 5.3.2).  Without `base` (an LTI
     start drawn at random; the least-squares start is ``init_ls``): A_0 =
     a0 I, B_0 and C_0 ~ N(0, bc_std^2), everything else zero.
     With `base` (an LPV restart): M_0 from base; the B and C blocks of M_1
     ~ N(0, m1_std^2) and its A block zero, so that A(p) = A_0 keeps the start's
-    spectrum; network weights by Xavier's uniform rule, biases zero."""
+    spectrum; network weights by Xavier's uniform rule (scaled by net_scale),
+    biases zero."""
     rng = np.random.default_rng(seed)
     L = layout(nx)
     nz = nx + 3
@@ -174,7 +175,7 @@ def initial_theta(nx: int, seed: int, base=None, m1_std: float = 1e-2, a0: float
     M1[nx:, :nx] = rng.normal(0.0, m1_std, (3, nx))
     th[L["M1"]] = M1.ravel()
     for name, fan_in, fan_out in (("W1", nz, 4), ("W2", 4, 4), ("w3", 4, 1)):
-        lim = np.sqrt(6.0 / (fan_in + fan_out))
+        lim = net_scale * np.sqrt(6.0 / (fan_in + fan_out))
         th[L[name]] = rng.uniform(-lim, lim, L[name].stop - L[name].start)
     th[L["b1"]] = th[L["b2"]] = th[L["b3"]] = 0.0
     return th.astype(np.float32)
