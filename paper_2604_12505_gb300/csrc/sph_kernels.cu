@@ -68,9 +68,14 @@ __global__ void __launch_bounds__(Shape<TX, TY>::THREADS, TAN ? 1 : Shape<TX, TY
     }
     const bool staged = stage_tile<TX, TY, false, TAN>(S, T, buf, cx0, cy0, sm);
     save_stage(sm, staged, stage_record<TX, TY>(S, blockIdx.x));
-    if (!staged) return;
-    const int n_own = sm.own_row[TY];
-    if (n_own == 0) return;
+    const int n_own = staged ? sm.own_row[TY] : 0;
+    if (n_own == 0) {
+        // a CTA that leaves without its dependency must not let the pass end
+        // before the body update: the first CTA always waits (the force pass,
+        // which depends on this one, reads what the body update writes)
+        if (early && blockIdx.x == 0) pdl_wait();
+        return;
+    }
 
     const bool want_drho = eval && E.drho;
     // the fluid part of own particle t: Sf (Eq. 14's fluid sum), Df (the
